@@ -1,0 +1,287 @@
+"""CPU oracle for LOWD with pruning and extraction (arXiv 2307.15969).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()`` and by
+the CPU-baseline leg of ``bench.py``, never by the library.  The arithmetic lives in
+``lowd_oracle.c`` (plain sequential C: double precision for Algorithm 1, exact integers
+for weights, degrees and densities); this module compiles it with gcc and marshals
+numpy arrays.  ``brute.py`` holds exhaustive solvers for tiny graphs.
+
+Parity status of each function is stated in its docstring; every function is pinned by
+``tests/test_oracle_*.py`` against closed forms, brute force, the exact min-cut solver,
+or invariants the paper proves.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lowd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liblowd_oracle.so")
+WEIGHT_SCALE = 1 << 20   # weighted graphs: integer units of 2^-20
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, -O2, no target-specific flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        P = C.c_void_p
+        i32, i64 = C.c_int32, C.c_int64
+        lib.orc_canonicalize.restype = i64
+        lib.orc_canonicalize.argtypes = [i32, i64, P, P, P, P, P, P, P]
+        lib.orc_degrees.argtypes = [i32, i64, P, P, P, P]
+        lib.orc_degree_order.argtypes = [i32, P, i32, P]
+        lib.orc_prune.restype = i32
+        lib.orc_prune.argtypes = [i32, i64, P, P, P, i32, P, P, P]
+        lib.orc_lowd_update.restype = C.c_double
+        lib.orc_lowd_update.argtypes = [P, P, P, P]
+        lib.orc_lowd_init.argtypes = [i32, i64, P, P, P, P, P, P]
+        lib.orc_lowd_iterate.argtypes = [i32, i64, P, P, P, i32, P, P, P, P]
+        lib.orc_extract.restype = i32
+        lib.orc_extract.argtypes = [i32, i64, P, P, P, P, P, P]
+        lib.orc_greedy.argtypes = [i32, i64, P, P, P, P, P]
+        lib.orc_densest_flow.restype = i32
+        lib.orc_densest_flow.argtypes = [i32, i64, P, P, P, P, P, P]
+        lib.orc_ldd.restype = i32
+        lib.orc_ldd.argtypes = [i32, i64, P, P, P, P, P, P]
+        lib.orc_load_stats.argtypes = [i32, P, P]
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+# ----------------------------------------------------------------------------- input
+
+def canonicalize(n, u, v, w=None):
+    """Undirected, loop-free, duplicate-free edges sorted by (lo, hi); a repeated pair
+    keeps its first weight (Sec. IV: multiple edges and self-loops removed, direction
+    ignored).  Raises ValueError on a self-loop or an id outside [0, n)."""
+    lib = _load()
+    u = _c(u, np.int32); v = _c(v, np.int32)
+    m = u.shape[0]
+    wd = None if w is None else _c(w, np.float64)
+    ou = np.empty(max(m, 1), np.int32); ov = np.empty(max(m, 1), np.int32)
+    ow = np.empty(max(m, 1), np.float64)
+    ndup = np.zeros(1, np.int64)
+    r = lib.orc_canonicalize(n, m, _p(u), _p(v), _p(wd), _p(ou), _p(ov), _p(ow), _p(ndup))
+    if r == -1:
+        raise ValueError("node id out of range")
+    if r == -2:
+        raise ValueError("self-loop")
+    if r < 0:
+        raise MemoryError
+    return ou[:r].copy(), ov[:r].copy(), (None if w is None else ow[:r].copy()), int(ndup[0])
+
+
+def weight_units(m: int, w) -> tuple[np.ndarray, int]:
+    """Integer weight units and their scale: unit weights -> (1, scale 1); weighted ->
+    (w * 2^20, scale 2^20), requiring every weight to lie on the 2^-20 grid."""
+    if w is None:
+        return np.ones(m, np.int64), 1
+    x = np.asarray(w, np.float64) * WEIGHT_SCALE
+    r = np.rint(x)
+    if not np.all(r == x) or np.any(r <= 0):
+        raise ValueError("weights must be positive multiples of 2^-20")
+    return r.astype(np.int64), WEIGHT_SCALE
+
+
+# ----------------------------------------------------------------------------- pruning
+
+def degrees(n, u, v, wu):
+    lib = _load()
+    deg = np.zeros(n, np.int64)
+    u = _c(u, np.int32); v = _c(v, np.int32); wu = _c(wu, np.int64)
+    lib.orc_degrees(n, u.shape[0], _p(u), _p(v), _p(wu), _p(deg))
+    return deg
+
+
+def degree_order(deg, weighted: bool):
+    """Nodes by degree ascending, ties by id (the counting sort of Sec. III-D)."""
+    lib = _load()
+    deg = _c(deg, np.int64)
+    perm = np.empty(deg.shape[0], np.int32)
+    lib.orc_degree_order(deg.shape[0], _p(deg), int(bool(weighted)), _p(perm))
+    return perm
+
+
+def prune(n, u, v, wu, weighted: bool):
+    """Algorithm 2's pruning loop in synchronous rounds.  Returns
+    dict(removal_round [n] (-1 kept, else 1-based round), rounds, W (units), N)."""
+    lib = _load()
+    u = _c(u, np.int32); v = _c(v, np.int32); wu = _c(wu, np.int64)
+    if not weighted and u.shape[0] and not np.all(wu == 1):
+        raise ValueError("unweighted pruning expects unit weights")
+    rr = np.empty(n, np.int32)
+    W = np.zeros(1, np.int64); N = np.zeros(1, np.int32)
+    rounds = lib.orc_prune(n, u.shape[0], _p(u), _p(v), _p(wu), int(bool(weighted)),
+                           _p(rr), _p(W), _p(N))
+    if rounds < 0:
+        raise MemoryError
+    return dict(removal_round=rr, rounds=int(rounds), W=int(W[0]), N=int(N[0]))
+
+
+def compact(n, u, v, w, keep_mask):
+    """Sub-graph induced by the kept nodes: survivors relabelled by ascending original
+    id, edges with both ends kept in their original order (Alg. 2: remove the pruned
+    nodes and their edges).  Returns (n_H, u_H, v_H, w_H, map H-id -> original id)."""
+    keep_mask = np.asarray(keep_mask, bool)
+    ids = np.nonzero(keep_mask)[0].astype(np.int32)
+    newid = np.full(n, -1, np.int64)
+    newid[ids] = np.arange(ids.shape[0])
+    ke = keep_mask[u] & keep_mask[v]
+    uh = newid[np.asarray(u)[ke]].astype(np.int32)
+    vh = newid[np.asarray(v)[ke]].astype(np.int32)
+    wh = None if w is None else np.asarray(w)[ke]
+    return int(ids.shape[0]), uh, vh, wh, ids
+
+
+# ----------------------------------------------------------------------------- Algorithm 1
+
+def lowd_update(lu, lv, fu, fv):
+    """One application of Algorithm 1's loop body to an edge (u, v).
+    Returns (lu, lv, fu, fv, d)."""
+    lib = _load()
+    a = np.array([lu, lv, fu, fv], np.float64)
+    d = lib.orc_lowd_update(_p(a[0:]), _p(a[1:]), _p(a[2:]), _p(a[3:]))
+    return float(a[0]), float(a[1]), float(a[2]), float(a[3]), float(d)
+
+
+class LowdState:
+    """Algorithm 1's state: the split vector f (f_e(u) and f_e(v) for every edge
+    e = (u, v), u < v) and the node loads l."""
+
+    def __init__(self, n, u, v, w=None):
+        lib = _load()
+        self.n = int(n)
+        self.u = _c(u, np.int32)
+        self.v = _c(v, np.int32)
+        self.m = int(self.u.shape[0])
+        self.w = np.ones(self.m) if w is None else _c(w, np.float64)
+        self.fu = np.empty(self.m); self.fv = np.empty(self.m); self.l = np.empty(self.n)
+        lib.orc_lowd_init(self.n, self.m, _p(self.u), _p(self.v), _p(self.w),
+                          _p(self.fu), _p(self.fv), _p(self.l))
+        self.iters = 0
+
+    def iterate(self, T: int, order=None, record_sumsq: bool = False):
+        """T passes of the edge loop in ``order`` (edge ids), default 0..m-1."""
+        lib = _load()
+        od = None if order is None else _c(order, np.int32)
+        if od is not None and od.shape[0] != self.m:
+            raise ValueError("order must list every edge once")
+        ss = np.empty(max(T, 1)) if record_sumsq else None
+        lib.orc_lowd_iterate(self.n, self.m, _p(self.u), _p(self.v), _p(od), int(T),
+                             _p(self.fu), _p(self.fv), _p(self.l), _p(ss))
+        self.iters += T
+        return ss[:T] if record_sumsq else None
+
+    def stats(self):
+        """(sum l, sum l^2, max l)."""
+        lib = _load()
+        out = np.zeros(3)
+        lib.orc_load_stats(self.n, _p(self.l), _p(out))
+        return float(out[0]), float(out[1]), float(out[2])
+
+
+def extract(n, u, v, wu, loads):
+    """Algorithm 1's extraction.  Returns (S* ids ascending, W(S*) in units)."""
+    lib = _load()
+    u = _c(u, np.int32); v = _c(v, np.int32); wu = _c(wu, np.int64)
+    l = _c(loads, np.float64)
+    S = np.empty(max(n, 1), np.int32)
+    Wb = np.zeros(1, np.int64)
+    k = lib.orc_extract(n, u.shape[0], _p(u), _p(v), _p(wu), _p(l), _p(S), _p(Wb))
+    if k < 0:
+        raise MemoryError
+    return S[:k].copy(), int(Wb[0])
+
+
+# ----------------------------------------------------------------------------- exact solvers
+
+def greedy(n, u, v, wu):
+    """Algorithm 3 (Charikar's peeling).  Returns (removal order, W left after each)."""
+    lib = _load()
+    u = _c(u, np.int32); v = _c(v, np.int32); wu = _c(wu, np.int64)
+    order = np.empty(n, np.int32); Wa = np.empty(n, np.int64)
+    lib.orc_greedy(n, u.shape[0], _p(u), _p(v), _p(wu), _p(order), _p(Wa))
+    return order, Wa
+
+
+def densest_flow(n, u, v, wu):
+    """Exact rho* (as a Fraction in weight units) and the maximal densest set B_1
+    (bool mask), by min cuts (Goldberg's construction, Dinkelbach's iteration)."""
+    lib = _load()
+    u = _c(u, np.int32); v = _c(v, np.int32); wu = _c(wu, np.int64)
+    inS = np.zeros(max(n, 1), np.int8)
+    Wn = np.zeros(1, np.int64); kd = np.zeros(1, np.int64)
+    k = lib.orc_densest_flow(n, u.shape[0], _p(u), _p(v), _p(wu), _p(inS), _p(Wn), _p(kd))
+    if k < 0:
+        raise OverflowError("min-cut capacities exceed 64 bits")
+    return Fraction(int(Wn[0]), int(kd[0])), inS[:n].astype(bool)
+
+
+def ldd(n, u, v, wu):
+    """Exact locally-dense decomposition: shell index per node (1 = B_1) and the
+    shell loads lambda_i as Fractions in weight units."""
+    lib = _load()
+    u = _c(u, np.int32); v = _c(v, np.int32); wu = _c(wu, np.int64)
+    shell = np.zeros(max(n, 1), np.int32)
+    num = np.zeros(max(n, 1), np.int64); den = np.zeros(max(n, 1), np.int64)
+    k = lib.orc_ldd(n, u.shape[0], _p(u), _p(v), _p(wu), _p(shell), _p(num), _p(den))
+    if k < 0:
+        raise OverflowError("min-cut capacities exceed 64 bits")
+    lam = [Fraction(int(num[i]), int(den[i])) for i in range(k)]
+    return shell[:n].copy(), lam
+
+
+def ldd_loads(n, u, v, wu, scale: int = 1):
+    """The unique optimal loads l* (Properties 1-2): l*_x = lambda of x's shell."""
+    shell, lam = ldd(n, u, v, wu)
+    lamf = np.array([float(x) / scale for x in lam])
+    return lamf[shell - 1] if n else np.zeros(0), shell, lam
+
+
+# ----------------------------------------------------------------------------- full pipeline
+
+def solve(n, u, v, w=None, T: int = 100, prune_first: bool = True, order=None):
+    """Algorithm 2 with LOWD as the plug-in solver: prune, run T passes on the pruned
+    graph, extract.  Returns a dict with the pruned graph, loads and S* (original ids)."""
+    wu, scale = weight_units(u.shape[0], w)
+    weighted = w is not None
+    if prune_first:
+        pr = prune(n, u, v, wu, weighted)
+        keep = pr["removal_round"] < 0
+    else:
+        pr = None
+        keep = np.ones(n, bool)
+    nh, uh, vh, wh, idmap = compact(n, u, v, w, keep)
+    st = LowdState(nh, uh, vh, None if wh is None else np.asarray(wh, np.float64))
+    st.iterate(T, order=order)
+    whu, _ = weight_units(uh.shape[0], wh)
+    S, Wb = extract(nh, uh, vh, whu, st.l)
+    return dict(prune=pr, n_H=nh, u_H=uh, v_H=vh, w_H=wh, map=idmap, state=st,
+                S=idmap[S], W=Wb, k=int(S.shape[0]), scale=scale,
+                rho=(Wb / scale / S.shape[0]) if S.shape[0] else 0.0)
