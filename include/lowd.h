@@ -1,0 +1,222 @@
+/*
+ * lowd.h - C ABI of a GB300 (sm_103a) implementation of LOWD, the Locally Optimal
+ * Weight Distribution method for the edge-density densest subgraph problem
+ * (arXiv 2307.15969), with its pruning pre-process and its extraction step.
+ *
+ * The method (paper notation): an undirected graph G(V, E, W) with positive edge
+ * weights w_e.  Every edge e = (u, v) splits its weight between its ends,
+ * f_e(u) + f_e(v) = w_e, f >= 0; a node's load is l_u = sum of f_e(u) over its edges
+ * (tighter dual, Sec. III-B).  LOWD (Algorithm 1) starts from the equal split and
+ * repeatedly moves weight across each edge from the more loaded end to the less loaded
+ * one, as far as the split allows; the loads converge to the locally-dense
+ * decomposition (Theorem 2), and peeling nodes by load recovers the densest subgraph.
+ * Pruning (Algorithm 2) first removes every node whose degree is below the current
+ * density, in rounds, which keeps the densest subgraph (Theorem 3).
+ *
+ * Calls, in the order of the method:
+ *   lowd_load_graph   graph in, canonicalised on the GPU           (Sec. II, Sec. IV data)
+ *   lowd_prune        Algorithm 2's pruning loop                   (Sec. III-D, Alg. 2)
+ *   lowd_iterate      k passes of Algorithm 1's edge loop          (Alg. 1, Sec. III-A)
+ *   lowd_extract      sort by load, best prefix density            (Alg. 1 extraction)
+ *
+ * Conventions (all calls):
+ *   - Every call returns a lowd_status; nothing is thrown or aborted across the ABI.
+ *     After an error the handle stays valid and can still be freed.
+ *   - All GPU work runs on the CUDA stream given to lowd_load_graph (NULL = legacy
+ *     default stream).  A call that writes host memory synchronises that stream before
+ *     it returns; calls that write only device memory return without synchronising.
+ *   - Pointer arguments are host pointers unless the handle was created with
+ *     LOWD_MEM_DEVICE, in which case array arguments (inputs and outputs, never the
+ *     scalar out-parameters such as n_kept or stats) are device pointers.
+ *   - The handle owns all its device memory (allocated by load_graph and freed by
+ *     lowd_free).  The caller owns every array it passes.
+ *   - Edge ids, node ids and sizes are 32-bit: n < 2^31 and m < 2^31.
+ *   - One handle must not be used by two host threads at once.
+ */
+#ifndef LOWD_H
+#define LOWD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lowd_ctx* lowd_handle;
+
+typedef enum {
+    LOWD_OK = 0,
+    LOWD_ERR_INVALID_ARG = 1,     /* bad size, null pointer, self-loop, id out of range,
+                                     non-positive / non-finite weight */
+    LOWD_ERR_OUT_OF_MEMORY = 2,   /* device allocation failed */
+    LOWD_ERR_CUDA = 3,            /* any other CUDA runtime error (message kept per handle) */
+    LOWD_ERR_BAD_STATE = 4,       /* call out of order, e.g. lowd_prune after lowd_iterate */
+    LOWD_ERR_NOT_CONVERGED = 5,   /* rel_tol > 0 was not met within k passes (state valid) */
+    LOWD_ERR_INEXACT_WEIGHTS = 6, /* a weight is not a multiple of 2^-20 (see lowd_load_graph) */
+    LOWD_ERR_TOO_LARGE = 7        /* a size exceeds a documented limit of the call */
+} lowd_status;
+
+enum { LOWD_MEM_HOST = 0, LOWD_MEM_DEVICE = 1 };
+
+/* Load-time flags (bit set). */
+enum {
+    LOWD_LOAD_ALLOW_INEXACT = 1   /* accept weights off the 2^-20 grid: they are rounded to it
+                                     for pruning and extraction sums, kept as given for LOWD */
+};
+
+/* Options of lowd_iterate; a zero-initialised struct gives the defaults. */
+typedef struct {
+    int32_t check_every;  /* >0: every check_every passes, re-derive the loads from the
+                             splits in FP64 and evaluate the stop test (default 0: no checks) */
+    double  rel_tol;      /* >0: stop once (D - rho(S))/rho(S) <= rel_tol at a check, where
+                             D = max load (an upper bound on rho*, Sec. III-B) and S the
+                             best prefix of the load order (default 0: run all k passes) */
+    int32_t schedule;     /* 0 = automatic; 1 = one-CTA shared-memory sweep (node count
+                             must fit shared memory); 2 = grid sweep over matchings */
+    int32_t reserved;
+} lowd_options;
+
+/* Statistics of the state after lowd_iterate (FP64, from loads re-derived from the
+ * splits when a check ran, else from the FP32 loads). */
+typedef struct {
+    int32_t iters_done;   /* total passes run on this handle so far */
+    int32_t checks_done;  /* checks evaluated by this call */
+    double  sum_load;     /* sum of l (equals the total edge weight, Sec. III-B) */
+    double  sum_load_sq;  /* sum of l^2, the QP objective of Sec. III-C */
+    double  max_load;     /* D = max l, an upper bound on rho* (Sec. III-B) */
+    double  rho_best;     /* density of the best load-ordered prefix at the last check */
+    int32_t best_size;    /* its size */
+    int32_t converged;    /* 1 if rel_tol was met */
+} lowd_stats;
+
+/* Sizes of the current graph and of its conflict-free schedule. */
+typedef struct {
+    int32_t n_orig;       /* nodes of the loaded graph G */
+    int32_t n;            /* nodes of the current graph (G, or H after lowd_prune) */
+    int64_t m_orig;       /* edges of G after canonicalisation */
+    int64_t m;            /* edges of the current graph */
+    int64_t duplicates;   /* input pairs dropped as repeats by lowd_load_graph */
+    int32_t weighted;     /* 1 if weights were given */
+    int32_t pruned;       /* 1 after lowd_prune */
+    int32_t classes;      /* colour classes of the schedule (0 before lowd_iterate) */
+    int32_t schedule;     /* schedule in use: 1 one-CTA shared memory, 2 grid matchings */
+    int32_t max_degree;   /* maximum (unweighted) degree of the current graph */
+    int32_t prune_rounds; /* rounds lowd_prune ran */
+} lowd_info;
+
+/*
+ * lowd_load_graph - build a handle on the undirected graph G(V, E, W) of Sec. II.
+ *   n        number of nodes, ids 0..n-1 (1 <= n < 2^31)
+ *   m        number of input pairs (0 <= m < 2^31)
+ *   u, v     endpoint arrays [m]; direction is ignored, repeated pairs are merged
+ *            keeping the first occurrence's weight (the paper removes multiple edges
+ *            and self-loops from its datasets, Sec. IV); a self-loop (u == v) or an id
+ *            outside [0, n) is rejected with LOWD_ERR_INVALID_ARG
+ *   w        weights [m] (> 0, finite), or NULL for unit weights (unweighted graph)
+ *   mem      LOWD_MEM_HOST or LOWD_MEM_DEVICE: where u, v, w and every later array
+ *            argument of this handle live
+ *   flags    0 or LOWD_LOAD_ALLOW_INEXACT
+ *   stream   cudaStream_t (as void*) on which all work of this handle runs
+ *   out      receives the handle (NULL on error)
+ * Weights must be multiples of 2^-20 (they are then exact FP32 values and every
+ * degree, W(H) and prefix weight is an exact 64-bit integer), else
+ * LOWD_ERR_INEXACT_WEIGHTS unless LOWD_LOAD_ALLOW_INEXACT is set.
+ * Inputs are copied; the caller may free them when the call returns.
+ */
+lowd_status lowd_load_graph(int32_t n, int64_t m, const int32_t* u, const int32_t* v,
+                            const float* w, int32_t mem, int32_t flags, void* stream,
+                            lowd_handle* out);
+
+/*
+ * lowd_prune - Algorithm 2's pruning loop (Sec. III-D): delta = rho(H) = W(H)/|H|;
+ * remove, all at once, every node u of H with d_H(u) < delta (strict, exact integer
+ * test d_H(u)*|H| < W(H)) and its edges; repeat until no node is removed.  d_H is the
+ * weighted degree for weighted graphs.  The nodes are first ordered by degree with a
+ * counting sort (Sec. III-D); lowd_get_prune_info returns that order.  Afterwards the
+ * handle's current graph is H: survivors renumbered by ascending original id, edges
+ * kept in their original order.  Must be called before lowd_iterate (else
+ * LOWD_ERR_BAD_STATE); may be called once.
+ *   n_kept, m_kept, rounds   host out-parameters (may be NULL)
+ */
+lowd_status lowd_prune(lowd_handle h, int32_t* n_kept, int64_t* m_kept, int32_t* rounds);
+
+/*
+ * lowd_iterate - k passes of Algorithm 1's edge loop (its lines after the
+ * initialisation) over the current graph.  The first call initialises
+ * f_e(u) = f_e(v) = w_e/2 and the loads (Algorithm 1's first loops) and builds the
+ * conflict-free schedule: a proper edge colouring, so every colour class is a matching
+ * and updating its edges in parallel equals updating them one after another.  A pass
+ * visits the classes in order; lowd_get_edge_order gives the resulting edge order.
+ *   k     number of passes (>= 0)
+ *   opt   options (NULL = defaults)
+ *   st    host out-parameter (may be NULL)
+ * Returns LOWD_ERR_NOT_CONVERGED only when opt->rel_tol > 0 and it was not met; the
+ * state is valid and a further call continues the run.
+ */
+lowd_status lowd_iterate(lowd_handle h, int32_t k, const lowd_options* opt, lowd_stats* st);
+
+/*
+ * lowd_extract - Algorithm 1's extraction: order the current graph's nodes by load
+ * (ascending, ties by id), peel them from the lowest, and keep the densest set seen,
+ * replacing it only on a strictly higher density (so ties keep the larger set); the
+ * empty set is not a candidate.  Prefix weights are exact integers (2^-20 units), the
+ * comparison is exact.  Valid at any time after lowd_load_graph (before any pass the
+ * loads are the equal-split loads).
+ *   S        out: ids of S* in ORIGINAL numbering, ascending; capacity >= n_orig; may be NULL
+ *   S_size   host out: |S*|
+ *   rho      host out: W(S*)/|S*| as a double
+ *   loads    out [n_orig]: FP32 load of every original node; nodes removed by pruning
+ *            get 0; may be NULL
+ */
+lowd_status lowd_extract(lowd_handle h, int32_t* S, int32_t* S_size, double* rho, float* loads);
+
+/* ------------------------------------------------------------------ state and parity hooks */
+
+/* Current graph sizes and schedule.  info: host pointer. */
+lowd_status lowd_get_info(lowd_handle h, lowd_info* info);
+
+/* Current graph's edges in the handle's canonical order (lo < hi; sorted by (lo, hi)
+ * for G, original order for H), ids in the current numbering.  u, v: [m]; w: [m] or
+ * NULL (unit weights give 1). */
+lowd_status lowd_get_graph(lowd_handle h, int32_t* u, int32_t* v, float* w);
+
+/* Splits s_e = f_e(lo) of every current edge (f_e(hi) = w_e - s_e), in the canonical
+ * edge order: get [m] out, set [m] in (values are clamped to [0, w_e] and the loads are
+ * recomputed from them; used for checkpoints and warm starts).  Before the first
+ * lowd_iterate, get returns the equal split and set initialises from the given split. */
+lowd_status lowd_get_splits(lowd_handle h, float* s);
+lowd_status lowd_set_splits(lowd_handle h, const float* s);
+
+/* Current loads [n] (current numbering). */
+lowd_status lowd_get_loads(lowd_handle h, float* loads);
+
+/* Pruning details, original numbering: sort_perm [n_orig] = nodes ordered by degree
+ * ascending, ties by id (the counting sort); removal_round [n_orig] = 1-based round in
+ * which the node was removed, -1 if kept.  Either may be NULL.  LOWD_ERR_BAD_STATE
+ * before lowd_prune. */
+lowd_status lowd_get_prune_info(lowd_handle h, int32_t* sort_perm, int32_t* removal_round);
+
+/* The schedule: perm [m] lists the canonical edge ids in the order a pass updates them
+ * (class by class; inside a class by edge id); class_offsets [classes + 1].  Either may
+ * be NULL.  *classes (host) receives the class count.  LOWD_ERR_BAD_STATE before the
+ * first lowd_iterate. */
+lowd_status lowd_get_edge_order(lowd_handle h, int32_t* perm, int32_t* class_offsets,
+                                int32_t* classes);
+
+/* Release the handle and all its device memory.  NULL is ignored. */
+void lowd_free(lowd_handle h);
+
+/* Static text for a status code. */
+const char* lowd_status_string(lowd_status s);
+
+/* Text of the last CUDA error seen by this handle ("" if none). */
+const char* lowd_last_error(lowd_handle h);
+
+/* Number of CUDA kernels this library has launched in this process so far (all handles,
+ * all threads).  A diagnostic for benchmarks; it has no counterpart in the paper. */
+uint64_t lowd_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOWD_H */

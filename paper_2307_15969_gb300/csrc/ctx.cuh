@@ -1,0 +1,135 @@
+// Handle state and host-side helpers shared by the LOWD translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/lowd.h"
+#include "prims.cuh"
+
+// Shared-memory budget of the one-CTA sweep: loads of up to this many nodes are kept
+// in shared memory (4 bytes each) for the whole sweep.
+#define LOWD_SMEM_NODES 53248
+
+struct lowd_ctx {
+    cudaStream_t st = nullptr;
+    int mem = LOWD_MEM_HOST;
+    int flags = 0;
+    char err[256] = {0};
+
+    // loaded graph G
+    int32_t n0 = 0;
+    int64_t m0 = 0;
+    int64_t dup = 0;
+    int weighted = 0;
+    int inexact = 0;  // some input weight was off the 2^-20 grid (allowed by flag)
+
+    // current graph (G, or H after pruning): canonical order, lo < hi
+    int32_t n = 0;
+    int64_t m = 0;
+    int32_t* u = nullptr;
+    int32_t* v = nullptr;
+    float* w = nullptr;     // [m] weights, null for unit weights
+    int64_t* wu = nullptr;  // [m] weight units of 2^-20, null for unit weights
+    int32_t* map = nullptr; // [n] current id -> original id; null while current == G
+    int32_t max_deg = 0;
+
+    // pruning record (original numbering)
+    int pruned = 0;
+    int32_t prune_rounds = 0;
+    int32_t* sort_perm = nullptr;      // [n0]
+    int32_t* removal_round = nullptr;  // [n0]
+
+    // LOWD state, kept in schedule (class-major) order
+    int inited = 0;
+    int32_t iters = 0;
+    int sched = 0;             // 1 one-CTA shared memory, 2 grid matchings
+    int32_t C = 0;             // number of classes
+    int32_t* perm = nullptr;   // [m] class-major position -> canonical edge id
+    int32_t* coff = nullptr;   // [C+1] device class offsets
+    int32_t* coff_h = nullptr; // [C+1] host copy
+    uint32_t* cuv = nullptr;   // [m] packed (lo | hi << 16) when n <= 65536
+    int32_t* cu = nullptr;     // [m] endpoints in class-major order (n > 65536)
+    int32_t* cv = nullptr;
+    float* cw = nullptr;       // [m] weights in class-major order (weighted only)
+    float* cs = nullptr;       // [m] splits f_e(lo) in class-major order
+    float* l = nullptr;        // [n] loads
+    // grid schedule: launch plan built on the host from coff_h
+    int32_t n_big = 0;         // classes [0, n_big) run as grid launches
+
+    // scratch
+    void* tmp = nullptr;
+    size_t tmp_cap = 0;
+    double* d_stats = nullptr;  // FP64 accumulators for checks
+    int64_t* d_i64 = nullptr;   // small int64 scratch (16 entries)
+    int32_t* d_i32 = nullptr;   // small int32 scratch (16 entries)
+    int64_t* h_pin = nullptr;   // pinned host mirror of small scalars (16 entries)
+
+    lowd_status fail(cudaError_t e) {
+        snprintf(err, sizeof(err), "%s", cudaGetErrorString(e));
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? LOWD_ERR_OUT_OF_MEMORY : LOWD_ERR_CUDA;
+    }
+    lowd_status need_tmp(size_t bytes) {
+        if (bytes <= tmp_cap) return LOWD_OK;
+        if (tmp) cudaFree(tmp);
+        tmp = nullptr;
+        tmp_cap = 0;
+        size_t b = bytes + (bytes >> 3) + 4096;
+        cudaError_t e = cudaMalloc(&tmp, b);
+        if (e != cudaSuccess) return fail(e);
+        tmp_cap = b;
+        return LOWD_OK;
+    }
+};
+
+#define LOWD_CK(call)                                             \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return h->fail(e_);                \
+    } while (0)
+
+#define LOWD_CK_LAUNCH() LOWD_CK(cudaGetLastError())
+
+#define LOWD_TRY(call)                        \
+    do {                                      \
+        lowd_status s_ = (call);              \
+        if (s_ != LOWD_OK) return s_;         \
+    } while (0)
+
+template <class T>
+inline lowd_status dalloc(lowd_ctx* h, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+    if (e != cudaSuccess) { *p = nullptr; return h->fail(e); }
+    return LOWD_OK;
+}
+
+template <class T>
+inline void dfree(T** p) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+}
+
+// bytes to allocate for a radix sort + scans over n elements
+size_t lowd_sort_tmp_bytes(int64_t n);
+
+// graph.cu
+lowd_status lowd_graph_load(lowd_ctx* h, const int32_t* du, const int32_t* dv, const float* dw,
+                            int64_t m_in);
+lowd_status lowd_graph_prune(lowd_ctx* h, int32_t* rounds);
+lowd_status lowd_graph_max_degree(lowd_ctx* h);
+
+// sweep.cu
+lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_splits_canon);
+lowd_status lowd_sweep_run(lowd_ctx* h, int32_t k, const lowd_options* opt, lowd_stats* st);
+lowd_status lowd_sweep_rederive(lowd_ctx* h, double* stats3);
+lowd_status lowd_sweep_splits_canonical(lowd_ctx* h, float* out_dev);
+lowd_status lowd_sweep_load_canonical(lowd_ctx* h, const float* splits_dev);
+
+// extract.cu
+lowd_status lowd_extract_best(lowd_ctx* h, const float* loads_dev, int32_t* S_dev_current,
+                              int32_t* S_size, int64_t* W_best);

@@ -1,0 +1,180 @@
+// Algorithm 1's extraction on the GPU: order nodes by load, peel from the lowest, keep
+// the densest set seen.  Peeling from the lowest load visits exactly the prefixes
+// S_k = {the k highest nodes in (load, id) order}, k = n..1, and replaces the best set
+// only on a strictly higher density, so the answer is the largest k maximising
+// W(S_k)/k.  W(S_k) is computed for every k at once: each edge contributes its weight to
+// the prefix that first contains both of its ends, bucket max(pos_a, pos_b) of the
+// descending order, and an inclusive scan of the buckets gives W(S_k).  All weights
+// are integer 2^-20 units, so the sums are exact and the comparison
+// W_a * k_b > W_b * k_a is done exactly in 128 bits.
+#include "ctx.cuh"
+#include "prims.cuh"
+
+using namespace lowd;
+
+namespace {
+
+constexpr int kT = 256;
+
+inline unsigned grid_for(int64_t n) {
+    int64_t b = (n + kT - 1) / kT;
+    if (b > 152 * 32) b = 152 * 32;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+// descending-load key: larger load -> smaller key; values start as n-1..0 so that the
+// stable sort leaves equal loads in descending id order
+__global__ void k_load_keys(const float* __restrict__ l, int32_t n, uint32_t* __restrict__ key,
+                            int32_t* __restrict__ val) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t x = n - 1 - (int32_t)i;
+        float f = l[x] + 0.0f;  // -0 -> +0
+        uint32_t b = __float_as_uint(f);
+        uint32_t ord = (b & 0x80000000u) ? ~b : (b | 0x80000000u);  // ascending order of floats
+        key[i] = ~ord;
+        val[i] = x;
+    }
+}
+
+__global__ void k_positions(const int32_t* __restrict__ order, int32_t n, int32_t* __restrict__ pos) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        pos[order[i]] = (int32_t)i;
+}
+
+__global__ void k_edge_buckets(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                               const int64_t* __restrict__ wu, int64_t m,
+                               const int32_t* __restrict__ pos, unsigned long long* __restrict__ bucket) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t p = max(pos[u[e]], pos[v[e]]);
+        atomicAdd(&bucket[p], wu ? (unsigned long long)wu[e] : 1ull);
+    }
+}
+
+struct Best {
+    int64_t W;  // W(S_k) in units
+    int64_t k;  // |S_k|
+};
+
+// a better than b: W_a/k_a > W_b/k_b, ties to the larger set
+__device__ __forceinline__ bool better(const Best& a, const Best& b) {
+    __int128 l = (__int128)a.W * (__int128)b.k;
+    __int128 r = (__int128)b.W * (__int128)a.k;
+    if (l != r) return l > r;
+    return a.k > b.k;
+}
+
+__device__ __forceinline__ Best shfl_best(const Best& x, int o) {
+    Best y;
+    y.W = __shfl_xor_sync(0xffffffffu, x.W, o);
+    y.k = __shfl_xor_sync(0xffffffffu, x.k, o);
+    return y;
+}
+
+// prefix weights W(S_k) = scan[k-1] + bucket[k-1] (inclusive); per-block best
+__global__ void k_best_prefix(const int64_t* __restrict__ excl, const unsigned long long* __restrict__ bucket,
+                              int32_t n, Best* __restrict__ part) {
+    Best b{0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        Best c{excl[i] + (int64_t)bucket[i], i + 1};
+        if (b.k == 0 || better(c, b)) b = c;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        Best y = shfl_best(b, o);
+        if (y.k != 0 && (b.k == 0 || better(y, b))) b = y;
+    }
+    __shared__ Best sh[kT / 32];
+    if (lane_id() == 0) sh[warp_id()] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Best r = sh[0];
+        for (int wv = 1; wv < (int)(blockDim.x >> 5); ++wv)
+            if (sh[wv].k != 0 && (r.k == 0 || better(sh[wv], r))) r = sh[wv];
+        part[blockIdx.x] = r;
+    }
+}
+
+__global__ void k_best_final(const Best* __restrict__ part, int32_t np, Best* __restrict__ out) {
+    if (threadIdx.x != 0) return;
+    Best r{0, 0};
+    for (int i = 0; i < np; ++i)
+        if (part[i].k != 0 && (r.k == 0 || better(part[i], r))) r = part[i];
+    *out = r;
+}
+
+__global__ void k_in_best(const int32_t* __restrict__ pos, int32_t n, const Best* __restrict__ best,
+                          int32_t* __restrict__ flag) {
+    int64_t k = best->k;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = pos[i] < k ? 1 : 0;
+}
+
+__global__ void k_emit_members(const int32_t* __restrict__ flag, const int32_t* __restrict__ fpos,
+                               int32_t n, const int32_t* __restrict__ map, int32_t* __restrict__ S) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) S[fpos[i]] = map ? map[i] : (int32_t)i;
+}
+
+}  // namespace
+
+// Best prefix of the load order on the current graph.  S_dev (device, may be null)
+// receives the members in ascending ORIGINAL ids.  *S_size and *W_best are host values.
+lowd_status lowd_extract_best(lowd_ctx* h, const float* loads_dev, int32_t* S_dev,
+                              int32_t* S_size, int64_t* W_best) {
+    cudaStream_t st = h->st;
+    const int32_t n = h->n;
+    const int64_t m = h->m;
+    uint32_t* key[2] = {nullptr, nullptr};
+    int32_t* val[2] = {nullptr, nullptr};
+    int32_t *pos = nullptr, *flag = nullptr, *fpos = nullptr;
+    unsigned long long* bucket = nullptr;
+    int64_t* excl = nullptr;
+    Best* part = nullptr;
+    lowd_status s = LOWD_OK;
+    auto cleanup = [&]() {
+        dfree(&key[0]); dfree(&key[1]); dfree(&val[0]); dfree(&val[1]); dfree(&pos);
+        dfree(&flag); dfree(&fpos); dfree(&bucket); dfree(&excl); dfree(&part);
+    };
+    do {
+        if ((s = h->need_tmp(lowd_sort_tmp_bytes(m > n ? m : n)))) break;
+        if ((s = dalloc(h, &key[0], n))) break;
+        if ((s = dalloc(h, &key[1], n))) break;
+        if ((s = dalloc(h, &val[0], n))) break;
+        if ((s = dalloc(h, &val[1], n))) break;
+        if ((s = dalloc(h, &pos, n))) break;
+        if ((s = dalloc(h, &bucket, n))) break;
+        if ((s = dalloc(h, &excl, n))) break;
+        const unsigned nb = grid_for(n);
+        if ((s = dalloc(h, &part, nb + 1))) break;
+        LOWD_LAUNCH(k_load_keys, grid_for(n), kT, 0, st, loads_dev, n, key[0], val[0]);
+        int cur = radix_sort_pairs<uint32_t, int32_t>(key[0], val[0], key[1], val[1], n, 32, h->tmp, st);
+        LOWD_LAUNCH(k_positions, grid_for(n), kT, 0, st, val[cur], n, pos);
+        cudaMemsetAsync(bucket, 0, sizeof(unsigned long long) * (size_t)n, st);
+        if (m > 0) LOWD_LAUNCH(k_edge_buckets, grid_for(m), kT, 0, st, h->u, h->v, h->wu, m, pos, bucket);
+        scan_exclusive<int64_t>((const int64_t*)bucket, excl, n, nullptr, h->tmp, st);
+        LOWD_LAUNCH(k_best_prefix, nb, kT, 0, st, excl, bucket, n, part);
+        LOWD_LAUNCH(k_best_final, 1, 32, 0, st, part, (int32_t)nb, part + nb);
+        if (S_dev) {
+            if ((s = dalloc(h, &flag, n))) break;
+            if ((s = dalloc(h, &fpos, n))) break;
+            LOWD_LAUNCH(k_in_best, grid_for(n), kT, 0, st, pos, n, part + nb, flag);
+            scan_exclusive<int32_t>(flag, fpos, n, nullptr, h->tmp, st);
+            LOWD_LAUNCH(k_emit_members, grid_for(n), kT, 0, st, flag, fpos, n, h->map, S_dev);
+        }
+        Best b;
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&b, part + nb, sizeof(Best), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { s = h->fail(e); break; }
+        if (S_size) *S_size = (int32_t)b.k;
+        if (W_best) *W_best = b.W;
+    } while (0);
+    cleanup();
+    return s;
+}

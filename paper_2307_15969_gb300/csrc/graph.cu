@@ -1,0 +1,496 @@
+// Graph input and Algorithm 2 (pruning) on the GPU.
+//
+//  - load: validation, canonical (lo, hi) keys, stable radix sort, removal of repeated
+//    pairs keeping the first occurrence (the paper drops multiple edges and self-loops
+//    and ignores direction, Sec. IV);
+//  - prune: weighted degrees in exact 2^-20 units, the counting sort of nodes by degree
+//    (Sec. III-D), then synchronous rounds of Algorithm 2: every node with
+//    d_H(u) * |H| < W(H) is removed at once, its edges subtract their weight from the
+//    surviving ends, and the bound is recomputed; finally H is compacted with its nodes
+//    renumbered by ascending original id and its edges in their original order.
+#include "ctx.cuh"
+#include "prims.cuh"
+
+using namespace lowd;
+
+namespace {
+
+constexpr int kT = 256;
+constexpr double kUnit = 1048576.0;  // 2^20 weight units per 1.0
+
+
+enum { ERR_RANGE = 1, ERR_LOOP = 2, ERR_WEIGHT = 4, ERR_GRID = 8, UNSORTED = 16 };
+
+// One pass over the input pairs: range, loop and weight checks, canonical key
+// lo * n + hi, and whether the input is already strictly increasing in that key.
+__global__ void k_check_keys(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                             const float* __restrict__ w, int64_t m, int32_t n,
+                             uint64_t* __restrict__ keys, uint32_t* __restrict__ idx,
+                             int32_t* __restrict__ err) {
+    int flags = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = u[e], b = v[e];
+        if (a < 0 || a >= n || b < 0 || b >= n) { flags |= ERR_RANGE; keys[e] = 0; idx[e] = (uint32_t)e; continue; }
+        if (a == b) flags |= ERR_LOOP;
+        uint64_t lo = (uint64_t)min(a, b), hi = (uint64_t)max(a, b);
+        uint64_t k = lo * (uint64_t)n + hi;
+        keys[e] = k;
+        idx[e] = (uint32_t)e;
+        if (w) {
+            float x = w[e];
+            if (!(x > 0.0f) || !isfinite(x)) flags |= ERR_WEIGHT;
+            double y = (double)x * kUnit;
+            if (y != rint(y)) flags |= ERR_GRID;
+        }
+        if (e > 0) {
+            int32_t pa = u[e - 1], pb = v[e - 1];
+            if (pa >= 0 && pa < n && pb >= 0 && pb < n) {
+                uint64_t pk = (uint64_t)min(pa, pb) * (uint64_t)n + (uint64_t)max(pa, pb);
+                if (!(pk < k)) flags |= UNSORTED;
+            }
+        }
+    }
+    flags = __reduce_or_sync(0xffffffffu, flags);
+    if (flags && lane_id() == 0) atomicOr(err, flags);
+}
+
+__global__ void k_first_flags(const uint64_t* __restrict__ keys, int64_t m, int32_t* __restrict__ f) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        f[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+__global__ void k_emit_unique(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ idx,
+                              const int32_t* __restrict__ first, const int32_t* __restrict__ pos,
+                              int64_t m, int32_t n, const float* __restrict__ w_in,
+                              int32_t* __restrict__ u, int32_t* __restrict__ v,
+                              float* __restrict__ w, int64_t* __restrict__ wu) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (first && !first[i]) continue;
+        int64_t p = pos ? pos[i] : i;
+        uint64_t k = keys[i];
+        u[p] = (int32_t)(k / (uint64_t)n);
+        v[p] = (int32_t)(k % (uint64_t)n);
+        if (w_in) {
+            float x = w_in[idx[i]];
+            w[p] = x;
+            double y = rint((double)x * kUnit);
+            wu[p] = y < 1.0 ? 1 : (int64_t)y;
+        }
+    }
+}
+
+// Weighted degree in units (unit weights count 1 per edge) and unweighted degree.
+__global__ void k_degrees(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                          const int64_t* __restrict__ wu, int64_t m,
+                          unsigned long long* __restrict__ deg, int32_t* __restrict__ cnt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = u[e], b = v[e];
+        unsigned long long x = wu ? (unsigned long long)wu[e] : 1ull;
+        if (deg) { atomicAdd(&deg[a], x); atomicAdd(&deg[b], x); }
+        if (cnt) { atomicAdd(&cnt[a], 1); atomicAdd(&cnt[b], 1); }
+    }
+}
+
+__global__ void k_max_i32(const int32_t* __restrict__ x, int64_t n, int32_t* __restrict__ out) {
+    int32_t best = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        best = max(best, x[i]);
+    best = __reduce_max_sync(0xffffffffu, best);
+    if (lane_id() == 0) atomicMax(out, best);
+}
+
+__global__ void k_max_u64(const unsigned long long* __restrict__ x, int64_t n,
+                          unsigned long long* __restrict__ out) {
+    unsigned long long best = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        best = max(best, x[i]);
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane_id() == 0) atomicMax(out, best);
+}
+
+__global__ void k_iota(int32_t* __restrict__ x, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = (int32_t)i;
+}
+
+__global__ void k_fill_i32(int32_t* __restrict__ x, int64_t n, int32_t val) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = val;
+}
+
+__device__ __forceinline__ bool below_bound(unsigned long long d, int64_t N, int64_t W) {
+    // d * N < W, exactly (d < 2^63, N < 2^31, W < 2^63)
+    unsigned __int128 lhs = (unsigned __int128)d * (unsigned __int128)(uint64_t)N;
+    return lhs < (unsigned __int128)(uint64_t)W;
+}
+
+// Round r of Algorithm 2, node side: among the listed live nodes, mark every node whose
+// current degree is below the density bound; count them.  keep[i] = 1 for survivors.
+__global__ void k_prune_mark(const int32_t* __restrict__ act, int64_t nact,
+                             const unsigned long long* __restrict__ deg, int64_t N, int64_t W,
+                             int32_t r, int32_t* __restrict__ rr, int32_t* __restrict__ keep,
+                             unsigned long long* __restrict__ removed) {
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nact;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t x = act[i];
+        bool rem = below_bound(deg[x], N, W);
+        if (rem) { rr[x] = r; ++c; }
+        keep[i] = rem ? 0 : 1;
+    }
+    c = warp_sum(c);
+    if (lane_id() == 0 && c) atomicAdd(removed, c);
+}
+
+// Round r, edge side: every live edge with an end removed in this round takes its weight
+// off W(H) and off the degree of a surviving end; edges with both ends alive are
+// appended (warp-aggregated) to the next round's edge list.
+__global__ void k_prune_edges(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                              const int64_t* __restrict__ ew, int64_t me, int32_t r,
+                              const int32_t* __restrict__ rr, unsigned long long* __restrict__ deg,
+                              unsigned long long* __restrict__ removedW,
+                              int32_t* __restrict__ nu, int32_t* __restrict__ nv,
+                              int64_t* __restrict__ nw, unsigned long long* __restrict__ ncount) {
+    unsigned long long acc = 0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < me;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = base + threadIdx.x;
+        bool ok = e < me;
+        bool keep = false;
+        int32_t a = 0, b = 0;
+        int64_t x = 0;
+        if (ok) {
+            a = eu[e]; b = ev[e];
+            x = ew ? ew[e] : 1;
+            bool ra = rr[a] == r, rb = rr[b] == r;
+            if (ra || rb) {
+                acc += (unsigned long long)x;
+                if (!ra) atomicAdd(&deg[a], (unsigned long long)(-x));
+                if (!rb) atomicAdd(&deg[b], (unsigned long long)(-x));
+            } else {
+                keep = true;
+            }
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, keep);
+        unsigned long long slot = 0;
+        if (lane_id() == 0 && bal) slot = atomicAdd(ncount, (unsigned long long)__popc(bal));
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (keep) {
+            unsigned long long p = slot + __popc(bal & ((1u << lane_id()) - 1u));
+            nu[p] = a; nv[p] = b;
+            if (nw) nw[p] = x;
+        }
+    }
+    acc = warp_sum(acc);
+    if (lane_id() == 0 && acc) atomicAdd(removedW, acc);
+}
+
+template <class T>
+__global__ void k_compact_by_flag(const T* __restrict__ in, const int32_t* __restrict__ flag,
+                                  const int32_t* __restrict__ pos, int64_t n, T* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) out[pos[i]] = in[i];
+}
+
+__global__ void k_keep_nodes(const int32_t* __restrict__ rr, int32_t n, int32_t* __restrict__ keep) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        keep[i] = rr[i] < 0 ? 1 : 0;
+}
+
+__global__ void k_node_map(const int32_t* __restrict__ keep, const int32_t* __restrict__ pos,
+                           int32_t n, const int32_t* __restrict__ old_map, int32_t* __restrict__ map) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (keep[i]) map[pos[i]] = old_map ? old_map[i] : (int32_t)i;
+}
+
+__global__ void k_keep_edges(const int32_t* __restrict__ u, const int32_t* __restrict__ v, int64_t m,
+                             const int32_t* __restrict__ keepn, int32_t* __restrict__ keepe) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        keepe[e] = (keepn[u[e]] && keepn[v[e]]) ? 1 : 0;
+}
+
+__global__ void k_emit_edges(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                             const float* __restrict__ w, const int64_t* __restrict__ wu, int64_t m,
+                             const int32_t* __restrict__ keepe, const int32_t* __restrict__ epos,
+                             const int32_t* __restrict__ npos, int32_t* __restrict__ ou,
+                             int32_t* __restrict__ ov, float* __restrict__ ow, int64_t* __restrict__ owu) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (!keepe[e]) continue;
+        int32_t p = epos[e];
+        ou[p] = npos[u[e]];
+        ov[p] = npos[v[e]];
+        if (w) { ow[p] = w[e]; owu[p] = wu[e]; }
+    }
+}
+
+inline unsigned grid_for(int64_t n) {
+    int64_t b = (n + kT - 1) / kT;
+    if (b > 152 * 32) b = 152 * 32;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+size_t lowd_sort_tmp_bytes(int64_t n) {
+    size_t a = radix_tmp_bytes(n);
+    size_t b = scan_tmp_bytes<int64_t>(n) + 256;
+    return a > b ? a : b;
+}
+
+// ------------------------------------------------------------------ load
+
+lowd_status lowd_graph_load(lowd_ctx* h, const int32_t* du, const int32_t* dv, const float* dw,
+                            int64_t m_in) {
+    cudaStream_t st = h->st;
+    const int32_t n = h->n0;
+    h->weighted = dw != nullptr;
+    uint64_t* keys[2] = {nullptr, nullptr};
+    uint32_t* idx[2] = {nullptr, nullptr};
+    int32_t* first = nullptr;
+    int32_t* pos = nullptr;
+    lowd_status s = LOWD_OK;
+    auto cleanup = [&]() {
+        dfree(&keys[0]); dfree(&keys[1]); dfree(&idx[0]); dfree(&idx[1]);
+        dfree(&first); dfree(&pos);
+    };
+    do {
+        if ((s = dalloc(h, &keys[0], m_in))) break;
+        if ((s = dalloc(h, &idx[0], m_in))) break;
+        if ((s = dalloc(h, &h->d_i32, 16))) break;
+        if ((s = dalloc(h, &h->d_i64, 16))) break;
+        if ((s = dalloc(h, &h->d_stats, 16))) break;
+        if (cudaMallocHost(&h->h_pin, 16 * sizeof(int64_t)) != cudaSuccess) { s = h->fail(cudaErrorMemoryAllocation); break; }
+        cudaMemsetAsync(h->d_i32, 0, 16 * sizeof(int32_t), st);
+        if (m_in > 0) {
+            LOWD_LAUNCH(k_check_keys, grid_for(m_in), kT, 0, st, du, dv, dw, m_in, n, keys[0], idx[0], h->d_i32);
+        }
+        if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
+        int32_t err = 0;
+        if (cudaMemcpyAsync(&err, h->d_i32, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
+        if (err & (ERR_RANGE | ERR_LOOP | ERR_WEIGHT)) {
+            snprintf(h->err, sizeof(h->err), "%s%s%s", (err & ERR_RANGE) ? "node id out of range; " : "",
+                     (err & ERR_LOOP) ? "self-loop; " : "", (err & ERR_WEIGHT) ? "non-positive or non-finite weight; " : "");
+            s = LOWD_ERR_INVALID_ARG;
+            break;
+        }
+        if ((err & ERR_GRID) && !(h->flags & LOWD_LOAD_ALLOW_INEXACT)) {
+            snprintf(h->err, sizeof(h->err), "weight not a multiple of 2^-20");
+            s = LOWD_ERR_INEXACT_WEIGHTS;
+            break;
+        }
+        h->inexact = (err & ERR_GRID) ? 1 : 0;
+        int cur = 0;
+        int64_t m = m_in;
+        const bool sorted = !(err & UNSORTED);
+        if (!sorted && m_in > 1) {
+            if ((s = dalloc(h, &keys[1], m_in))) break;
+            if ((s = dalloc(h, &idx[1], m_in))) break;
+            if ((s = h->need_tmp(lowd_sort_tmp_bytes(m_in)))) break;
+            int bits = bit_length_u64((uint64_t)n * (uint64_t)n - 1);
+            cur = radix_sort_pairs<uint64_t, uint32_t>(keys[0], idx[0], keys[1], idx[1], m_in, bits, h->tmp, st);
+            if ((s = dalloc(h, &first, m_in))) break;
+            if ((s = dalloc(h, &pos, m_in))) break;
+            LOWD_LAUNCH(k_first_flags, grid_for(m_in), kT, 0, st, keys[cur], m_in, first);
+            scan_exclusive<int32_t>(first, pos, m_in, h->d_i32 + 1, h->tmp, st);
+            int32_t mu = 0;
+            if (cudaMemcpyAsync(&mu, h->d_i32 + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
+            m = mu;
+        }
+        h->m0 = h->m = m;
+        h->dup = m_in - m;
+        h->n = n;
+        if ((s = dalloc(h, &h->u, m))) break;
+        if ((s = dalloc(h, &h->v, m))) break;
+        if (h->weighted) {
+            if ((s = dalloc(h, &h->w, m))) break;
+            if ((s = dalloc(h, &h->wu, m))) break;
+        }
+        if (m_in > 0)
+            LOWD_LAUNCH(k_emit_unique, grid_for(m_in), kT, 0, st, keys[cur], idx[cur], first, pos, m_in, n, dw,
+                                                         h->u, h->v, h->w, h->wu);
+        if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
+        s = lowd_graph_max_degree(h);
+    } while (0);
+    cleanup();
+    return s;
+}
+
+lowd_status lowd_graph_max_degree(lowd_ctx* h) {
+    cudaStream_t st = h->st;
+    int32_t* cnt = nullptr;
+    LOWD_TRY(dalloc(h, &cnt, h->n));
+    cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)h->n, st);
+    cudaMemsetAsync(h->d_i32 + 2, 0, sizeof(int32_t), st);
+    if (h->m > 0) LOWD_LAUNCH(k_degrees, grid_for(h->m), kT, 0, st, h->u, h->v, nullptr, h->m, nullptr, cnt);
+    LOWD_LAUNCH(k_max_i32, grid_for(h->n), kT, 0, st, cnt, h->n, h->d_i32 + 2);
+    int32_t md = 0;
+    cudaError_t e = cudaMemcpyAsync(&md, h->d_i32 + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(&cnt);
+    if (e != cudaSuccess) return h->fail(e);
+    h->max_deg = md;
+    return LOWD_OK;
+}
+
+// ------------------------------------------------------------------ Algorithm 2
+
+lowd_status lowd_graph_prune(lowd_ctx* h, int32_t* rounds_out) {
+    cudaStream_t st = h->st;
+    const int32_t n = h->n;
+    const int64_t m = h->m;
+    unsigned long long* deg = nullptr;
+    uint64_t* dkey[2] = {nullptr, nullptr};
+    int32_t* dval[2] = {nullptr, nullptr};
+    int32_t *act = nullptr, *act2 = nullptr, *keep = nullptr, *pos = nullptr;
+    int32_t *eu[2] = {nullptr, nullptr}, *ev[2] = {nullptr, nullptr};
+    int64_t* ew[2] = {nullptr, nullptr};
+    int32_t *keepe = nullptr, *epos = nullptr, *nmap = nullptr;
+    int32_t *nu = nullptr, *nv = nullptr;
+    float* nw = nullptr;
+    int64_t* nwu = nullptr;
+    lowd_status s = LOWD_OK;
+    auto cleanup = [&]() {
+        dfree(&deg); dfree(&dkey[0]); dfree(&dkey[1]); dfree(&dval[0]); dfree(&dval[1]);
+        dfree(&act); dfree(&act2); dfree(&keep); dfree(&pos);
+        dfree(&eu[0]); dfree(&eu[1]); dfree(&ev[0]); dfree(&ev[1]); dfree(&ew[0]); dfree(&ew[1]);
+        dfree(&keepe); dfree(&epos); dfree(&nmap); dfree(&nu); dfree(&nv); dfree(&nw); dfree(&nwu);
+    };
+    do {
+        if ((s = dalloc(h, &deg, n))) break;
+        if ((s = dalloc(h, &h->sort_perm, n))) break;
+        if ((s = dalloc(h, &h->removal_round, n))) break;
+        if ((s = h->need_tmp(lowd_sort_tmp_bytes(m > n ? m : n)))) break;
+        cudaMemsetAsync(deg, 0, sizeof(unsigned long long) * (size_t)n, st);
+        if (m > 0) LOWD_LAUNCH(k_degrees, grid_for(m), kT, 0, st, h->u, h->v, h->wu, m, deg, nullptr);
+        // W(G) = sum of degrees / 2 = sum of weights (units)
+        unsigned long long* dmax = (unsigned long long*)(h->d_i64 + 0);
+        cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), st);
+        LOWD_LAUNCH(k_max_u64, grid_for(n), kT, 0, st, deg, n, dmax);
+        // counting sort of nodes by degree (ascending, ties by id): LSD radix passes,
+        // each a counting sort on one 8-bit digit of the degree
+        if ((s = dalloc(h, &dkey[0], n))) break;
+        if ((s = dalloc(h, &dkey[1], n))) break;
+        if ((s = dalloc(h, &dval[0], n))) break;
+        if ((s = dalloc(h, &dval[1], n))) break;
+        cudaMemcpyAsync(dkey[0], deg, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+        LOWD_LAUNCH(k_iota, grid_for(n), kT, 0, st, dval[0], n);
+        if (cudaMemcpyAsync(h->h_pin, dmax, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
+        int bits = bit_length_u64((uint64_t)h->h_pin[0]);
+        int cur = radix_sort_pairs<uint64_t, int32_t>(dkey[0], dval[0], dkey[1], dval[1], n, bits, h->tmp, st);
+        cudaMemcpyAsync(h->sort_perm, dval[cur], sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+        LOWD_LAUNCH(k_fill_i32, grid_for(n), kT, 0, st, h->removal_round, n, -1);
+
+        // total weight W(G)
+        int64_t W = 0;
+        if (h->wu) {
+            // sum of units via the degree sum (each edge counted twice)
+            int64_t* tot = h->d_i64 + 2;
+            scan_exclusive<int64_t>((const int64_t*)deg, (int64_t*)dkey[1 - cur], n, tot, h->tmp, st);
+            if (cudaMemcpyAsync(h->h_pin, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
+            W = h->h_pin[0] / 2;
+        } else {
+            W = m;
+        }
+        int64_t N = n;
+
+        // live node list (degree order) and live edge list
+        if ((s = dalloc(h, &act, n))) break;
+        if ((s = dalloc(h, &act2, n))) break;
+        if ((s = dalloc(h, &keep, n))) break;
+        if ((s = dalloc(h, &pos, n))) break;
+        cudaMemcpyAsync(act, h->sort_perm, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+        int64_t nact = n;
+        if ((s = dalloc(h, &eu[1], m))) break;
+        if ((s = dalloc(h, &ev[1], m))) break;
+        if (h->wu && (s = dalloc(h, &ew[1], m))) break;
+        const int32_t* cu_ = h->u;
+        const int32_t* cv_ = h->v;
+        const int64_t* cw_ = h->wu;
+        int64_t me = m;
+        int nxt = 1;
+        int32_t r = 0;
+        unsigned long long* removed = (unsigned long long*)(h->d_i64 + 4);
+        unsigned long long* removedW = (unsigned long long*)(h->d_i64 + 5);
+        unsigned long long* ncount = (unsigned long long*)(h->d_i64 + 6);
+        while (N > 0) {
+            int32_t rnext = r + 1;
+            cudaMemsetAsync(h->d_i64 + 4, 0, 3 * sizeof(int64_t), st);
+            LOWD_LAUNCH(k_prune_mark, grid_for(nact), kT, 0, st, act, nact, deg, N, W, rnext, h->removal_round, keep, removed);
+            if (me > 0)
+                LOWD_LAUNCH(k_prune_edges, grid_for(me), kT, 0, st, cu_, cv_, cw_, me, rnext, h->removal_round, deg,
+                                                           removedW, eu[nxt], ev[nxt], ew[nxt], ncount);
+            if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
+            if (cudaMemcpyAsync(h->h_pin, h->d_i64 + 4, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
+            int64_t k = h->h_pin[0];
+            if (k == 0) break;  // the edge pass saw no removed end and kept every edge
+            r = rnext;
+            N -= k;
+            W -= h->h_pin[1];
+            cu_ = eu[nxt]; cv_ = ev[nxt]; cw_ = ew[nxt];
+            me = h->h_pin[2];
+            if (!eu[1 - nxt] && (s = dalloc(h, &eu[1 - nxt], m))) break;
+            if (!ev[1 - nxt] && (s = dalloc(h, &ev[1 - nxt], m))) break;
+            if (h->wu && !ew[1 - nxt] && (s = dalloc(h, &ew[1 - nxt], m))) break;
+            nxt = 1 - nxt;
+            // stable compaction of the live node list
+            scan_exclusive<int32_t>(keep, pos, nact, h->d_i32 + 3, h->tmp, st);
+            LOWD_LAUNCH(k_compact_by_flag<int32_t>, grid_for(nact), kT, 0, st, act, keep, pos, nact, act2);
+            int32_t* t = act; act = act2; act2 = t;
+            nact = N;
+        }
+        if (s) break;
+        h->prune_rounds = r;
+
+        // compaction to H: survivors by ascending id, edges in original order
+        if ((s = dalloc(h, &keepe, m))) break;
+        if ((s = dalloc(h, &epos, m))) break;
+        if ((s = dalloc(h, &nmap, N))) break;
+        LOWD_LAUNCH(k_keep_nodes, grid_for(n), kT, 0, st, h->removal_round, n, keep);
+        scan_exclusive<int32_t>(keep, pos, n, nullptr, h->tmp, st);
+        LOWD_LAUNCH(k_node_map, grid_for(n), kT, 0, st, keep, pos, n, h->map, nmap);
+        if (m > 0) LOWD_LAUNCH(k_keep_edges, grid_for(m), kT, 0, st, h->u, h->v, m, keep, keepe);
+        scan_exclusive<int32_t>(keepe, epos, m, h->d_i32 + 4, h->tmp, st);
+        if (cudaMemcpyAsync(h->h_pin, h->d_i32 + 4, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
+        int64_t mH = *(int32_t*)h->h_pin;
+        if ((s = dalloc(h, &nu, mH))) break;
+        if ((s = dalloc(h, &nv, mH))) break;
+        if (h->w) {
+            if ((s = dalloc(h, &nw, mH))) break;
+            if ((s = dalloc(h, &nwu, mH))) break;
+        }
+        if (m > 0)
+            LOWD_LAUNCH(k_emit_edges, grid_for(m), kT, 0, st, h->u, h->v, h->w, h->wu, m, keepe, epos, pos, nu, nv, nw, nwu);
+        if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
+        // swap in H
+        dfree(&h->u); dfree(&h->v); dfree(&h->w); dfree(&h->wu); dfree(&h->map);
+        h->u = nu; h->v = nv; h->w = nw; h->wu = nwu; h->map = nmap;
+        nu = nv = nullptr; nw = nullptr; nwu = nullptr; nmap = nullptr;
+        h->n = (int32_t)N;
+        h->m = mH;
+        h->pruned = 1;
+        if (rounds_out) *rounds_out = r;
+        s = lowd_graph_max_degree(h);
+    } while (0);
+    cleanup();
+    return s;
+}

@@ -1,0 +1,290 @@
+"""Python binding of the LOWD C ABI (include/lowd.h): argument marshalling only.
+
+Every function has the C name and forwards to ``liblowd.so``; no step of the method runs
+here.  Arrays may be numpy arrays (host mode) or CUDA torch tensors (device mode, chosen
+by the first array given to :func:`lowd_load_graph`); outputs come back in the same mode.
+The library must have been built (``python -m paper_2307_15969_gb300.build`` or
+``__graft_entry__.build()``); if it is missing, loading fails with an error rather than
+falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblowd.so")
+
+LOWD_OK = 0
+LOWD_ERR_INVALID_ARG = 1
+LOWD_ERR_OUT_OF_MEMORY = 2
+LOWD_ERR_CUDA = 3
+LOWD_ERR_BAD_STATE = 4
+LOWD_ERR_NOT_CONVERGED = 5
+LOWD_ERR_INEXACT_WEIGHTS = 6
+LOWD_ERR_TOO_LARGE = 7
+LOWD_MEM_HOST = 0
+LOWD_MEM_DEVICE = 1
+LOWD_LOAD_ALLOW_INEXACT = 1
+
+EXPORTED = (
+    "lowd_load_graph", "lowd_prune", "lowd_iterate", "lowd_extract", "lowd_get_info",
+    "lowd_get_graph", "lowd_get_splits", "lowd_set_splits", "lowd_get_loads",
+    "lowd_get_prune_info", "lowd_get_edge_order", "lowd_free", "lowd_status_string",
+    "lowd_last_error", "lowd_launch_count",
+)
+
+
+class lowd_options(C.Structure):
+    _fields_ = [("check_every", C.c_int32), ("rel_tol", C.c_double),
+                ("schedule", C.c_int32), ("reserved", C.c_int32)]
+
+
+class lowd_stats(C.Structure):
+    _fields_ = [("iters_done", C.c_int32), ("checks_done", C.c_int32), ("sum_load", C.c_double),
+                ("sum_load_sq", C.c_double), ("max_load", C.c_double), ("rho_best", C.c_double),
+                ("best_size", C.c_int32), ("converged", C.c_int32)]
+
+
+class lowd_info(C.Structure):
+    _fields_ = [("n_orig", C.c_int32), ("n", C.c_int32), ("m_orig", C.c_int64), ("m", C.c_int64),
+                ("duplicates", C.c_int64), ("weighted", C.c_int32), ("pruned", C.c_int32),
+                ("classes", C.c_int32), ("schedule", C.c_int32), ("max_degree", C.c_int32),
+                ("prune_rounds", C.c_int32)]
+
+
+class LowdError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {lowd_status_string(status)} ({status})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load liblowd.so and declare its signatures.  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"liblowd.so not built at {path}: run paper_2307_15969_gb300.build.build()")
+    lib = C.CDLL(path)
+    P, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    lib.lowd_load_graph.restype = i32
+    lib.lowd_load_graph.argtypes = [i32, i64, P, P, P, i32, i32, P, C.POINTER(P)]
+    lib.lowd_prune.restype = i32
+    lib.lowd_prune.argtypes = [P, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
+    lib.lowd_iterate.restype = i32
+    lib.lowd_iterate.argtypes = [P, i32, C.POINTER(lowd_options), C.POINTER(lowd_stats)]
+    lib.lowd_extract.restype = i32
+    lib.lowd_extract.argtypes = [P, P, C.POINTER(i32), C.POINTER(C.c_double), P]
+    lib.lowd_get_info.restype = i32
+    lib.lowd_get_info.argtypes = [P, C.POINTER(lowd_info)]
+    lib.lowd_get_graph.restype = i32
+    lib.lowd_get_graph.argtypes = [P, P, P, P]
+    lib.lowd_get_splits.restype = i32
+    lib.lowd_get_splits.argtypes = [P, P]
+    lib.lowd_set_splits.restype = i32
+    lib.lowd_set_splits.argtypes = [P, P]
+    lib.lowd_get_loads.restype = i32
+    lib.lowd_get_loads.argtypes = [P, P]
+    lib.lowd_get_prune_info.restype = i32
+    lib.lowd_get_prune_info.argtypes = [P, P, P]
+    lib.lowd_get_edge_order.restype = i32
+    lib.lowd_get_edge_order.argtypes = [P, P, P, C.POINTER(i32)]
+    lib.lowd_free.restype = None
+    lib.lowd_free.argtypes = [P]
+    lib.lowd_status_string.restype = C.c_char_p
+    lib.lowd_status_string.argtypes = [i32]
+    lib.lowd_last_error.restype = C.c_char_p
+    lib.lowd_last_error.argtypes = [P]
+    lib.lowd_launch_count.restype = C.c_uint64
+    lib.lowd_launch_count.argtypes = []
+    _lib = lib
+    return lib
+
+
+def lowd_status_string(status: int) -> str:
+    return load_library().lowd_status_string(int(status)).decode()
+
+
+def lowd_launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load_library().lowd_launch_count())
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+class Handle:
+    """An open LOWD handle (the C ``lowd_handle``) and the memory mode of its arrays."""
+
+    def __init__(self, ptr: int, device: bool, n0: int, stream):
+        self.ptr = C.c_void_p(ptr)
+        self.device = device
+        self.n0 = n0
+        self.stream = stream
+
+    def __del__(self):
+        try:
+            lowd_free(self)
+        except Exception:
+            pass
+
+    def _check(self, status: int, where: str):
+        if status != LOWD_OK:
+            detail = load_library().lowd_last_error(self.ptr).decode() if self.ptr else ""
+            raise LowdError(status, where, detail)
+
+    # array helpers: allocate an output in this handle's memory mode
+    def empty(self, n: int, dtype):
+        if self.device:
+            import torch
+            td = {np.int32: torch.int32, np.float32: torch.float32}[dtype]
+            return torch.empty(max(int(n), 1), dtype=td, device="cuda")
+        return np.empty(max(int(n), 1), dtype=dtype)
+
+    def ptr_of(self, a):
+        if a is None:
+            return None
+        if self.device:
+            if not _is_torch(a) or not a.is_cuda or not a.is_contiguous():
+                raise ValueError("device-mode handles take contiguous CUDA tensors")
+            return C.c_void_p(a.data_ptr())
+        if not isinstance(a, np.ndarray) or not a.flags.c_contiguous:
+            raise ValueError("host-mode handles take contiguous numpy arrays")
+        return a.ctypes.data_as(C.c_void_p)
+
+
+def lowd_load_graph(n: int, u, v, w=None, flags: int = 0, stream=None) -> Handle:
+    """Load an undirected graph; numpy arrays give a host-mode handle, CUDA tensors a
+    device-mode one.  ``stream`` is a torch.cuda.Stream (device mode; default: the
+    current stream) or None (legacy default stream)."""
+    lib = load_library()
+    device = _is_torch(u)
+    if device:
+        import torch
+        u = u.to(torch.int32).contiguous(); v = v.to(torch.int32).contiguous()
+        if w is not None:
+            w = w.to(torch.float32).contiguous()
+        st = stream if stream is not None else torch.cuda.current_stream()
+        sptr = C.c_void_p(st.cuda_stream)
+        pu, pv = C.c_void_p(u.data_ptr()), C.c_void_p(v.data_ptr())
+        pw = C.c_void_p(w.data_ptr()) if w is not None else None
+        m = int(u.numel())
+        keep = (u, v, w)
+    else:
+        u = np.ascontiguousarray(u, dtype=np.int32); v = np.ascontiguousarray(v, dtype=np.int32)
+        if w is not None:
+            w = np.ascontiguousarray(w, dtype=np.float32)
+        st = stream
+        sptr = C.c_void_p(stream.cuda_stream) if stream is not None else None
+        pu, pv = u.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p)
+        pw = w.ctypes.data_as(C.c_void_p) if w is not None else None
+        m = int(u.shape[0])
+        keep = (u, v, w)
+    if (v.numel() if device else v.shape[0]) != m or (w is not None and (w.numel() if device else w.shape[0]) != m):
+        raise ValueError("u, v, w must have the same length")
+    out = C.c_void_p()
+    s = lib.lowd_load_graph(int(n), m, pu, pv, pw, LOWD_MEM_DEVICE if device else LOWD_MEM_HOST,
+                            int(flags), sptr, C.byref(out))
+    del keep
+    if s != LOWD_OK:
+        raise LowdError(s, "lowd_load_graph")
+    return Handle(out.value, device, int(n), st)
+
+
+def lowd_prune(h: Handle):
+    """Algorithm 2's pruning; returns (n_kept, m_kept, rounds)."""
+    nk, mk, r = C.c_int32(), C.c_int64(), C.c_int32()
+    h._check(load_library().lowd_prune(h.ptr, C.byref(nk), C.byref(mk), C.byref(r)), "lowd_prune")
+    return nk.value, mk.value, r.value
+
+
+def lowd_iterate(h: Handle, k: int, check_every: int = 0, rel_tol: float = 0.0,
+                 schedule: int = 0, allow_not_converged: bool = True) -> dict:
+    """k LOWD passes; returns the lowd_stats fields as a dict (plus 'status')."""
+    o = lowd_options(int(check_every), float(rel_tol), int(schedule), 0)
+    st = lowd_stats()
+    s = load_library().lowd_iterate(h.ptr, int(k), C.byref(o), C.byref(st))
+    if s != LOWD_OK and not (allow_not_converged and s == LOWD_ERR_NOT_CONVERGED):
+        h._check(s, "lowd_iterate")
+    d = {f: getattr(st, f) for f, _ in lowd_stats._fields_}
+    d["status"] = s
+    return d
+
+
+def lowd_extract(h: Handle, want_loads: bool = True):
+    """Algorithm 1's extraction; returns (S* original ids ascending, rho*, loads [n_orig] or None)."""
+    S = h.empty(h.n0, np.int32)
+    loads = h.empty(h.n0, np.float32) if want_loads else None
+    k = C.c_int32()
+    rho = C.c_double()
+    h._check(load_library().lowd_extract(h.ptr, h.ptr_of(S), C.byref(k), C.byref(rho),
+                                         h.ptr_of(loads)), "lowd_extract")
+    return S[:k.value], rho.value, (loads[:h.n0] if loads is not None else None)
+
+
+def lowd_get_info(h: Handle) -> dict:
+    info = lowd_info()
+    h._check(load_library().lowd_get_info(h.ptr, C.byref(info)), "lowd_get_info")
+    return {f: getattr(info, f) for f, _ in lowd_info._fields_}
+
+
+def lowd_get_graph(h: Handle):
+    m = lowd_get_info(h)["m"]
+    u, v, w = h.empty(m, np.int32), h.empty(m, np.int32), h.empty(m, np.float32)
+    h._check(load_library().lowd_get_graph(h.ptr, h.ptr_of(u), h.ptr_of(v), h.ptr_of(w)), "lowd_get_graph")
+    return u[:m], v[:m], w[:m]
+
+
+def lowd_get_splits(h: Handle):
+    m = lowd_get_info(h)["m"]
+    s = h.empty(m, np.float32)
+    h._check(load_library().lowd_get_splits(h.ptr, h.ptr_of(s)), "lowd_get_splits")
+    return s[:m]
+
+
+def lowd_set_splits(h: Handle, s):
+    if h.device:
+        import torch
+        s = s.to(torch.float32).contiguous()
+    else:
+        s = np.ascontiguousarray(s, dtype=np.float32)
+    h._check(load_library().lowd_set_splits(h.ptr, h.ptr_of(s)), "lowd_set_splits")
+
+
+def lowd_get_loads(h: Handle):
+    n = lowd_get_info(h)["n"]
+    l = h.empty(n, np.float32)
+    h._check(load_library().lowd_get_loads(h.ptr, h.ptr_of(l)), "lowd_get_loads")
+    return l[:n]
+
+
+def lowd_get_prune_info(h: Handle):
+    perm, rr = h.empty(h.n0, np.int32), h.empty(h.n0, np.int32)
+    h._check(load_library().lowd_get_prune_info(h.ptr, h.ptr_of(perm), h.ptr_of(rr)), "lowd_get_prune_info")
+    return perm[:h.n0], rr[:h.n0]
+
+
+def lowd_get_edge_order(h: Handle):
+    info = lowd_get_info(h)
+    perm = h.empty(info["m"], np.int32)
+    offs = h.empty(info["classes"] + 1, np.int32)
+    c = C.c_int32()
+    h._check(load_library().lowd_get_edge_order(h.ptr, h.ptr_of(perm), h.ptr_of(offs), C.byref(c)),
+             "lowd_get_edge_order")
+    return perm[:info["m"]], offs[:c.value + 1]
+
+
+def lowd_free(h: Handle):
+    if h is not None and h.ptr and h.ptr.value:
+        load_library().lowd_free(h.ptr)
+        h.ptr = C.c_void_p(None)

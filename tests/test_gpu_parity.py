@@ -1,0 +1,344 @@
+"""GPU parity: the CUDA library against the CPU oracle, through the C ABI.
+
+Bars (bit-exact where the work is integer, tolerance where it is floating point):
+ - canonical edge list, counting-sort order, pruning rounds and the pruned graph H:
+   bit-exact;
+ - extraction: the GPU's S* and W(S*) equal the oracle's extraction run on the same FP32
+   loads (the order decision is taken in FP32 on both sides), bit-exact;
+ - same-order LOWD: the oracle (FP64) replays the GPU's edge order; loads agree within
+   LOAD_TOL * max load, the tolerance derived for FP32 passes;
+ - converged: loads within 1e-4 relative of the exact LDD loads, S* equal to the maximal
+   densest set from the min-cut solver, rho* within 1e-9 relative.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+LOAD_TOL = 1e-4   # relative to the largest load; FP32 passes, see the design doc
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_15969_gb300 import build
+    build.build()
+    import paper_2307_15969_gb300 as p
+    p.load_library()
+    return p
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def _np(x):
+    return x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+
+
+def _load(pkg, g, device, w=None, flags=0):
+    import torch
+    w = g.w if w is None else w
+    if device:
+        return pkg.lowd_load_graph(g.n, torch.from_numpy(np.ascontiguousarray(g.u)).cuda(),
+                                   torch.from_numpy(np.ascontiguousarray(g.v)).cuda(),
+                                   None if w is None else torch.from_numpy(np.asarray(w, np.float32)).cuda(),
+                                   flags=flags)
+    return pkg.lowd_load_graph(g.n, g.u, g.v, w, flags=flags)
+
+
+# ----------------------------------------------------------------------------- load
+
+@pytest.mark.parametrize("device", [False, True])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_load_canonicalises_like_the_oracle(pkg, orc, device, weighted):
+    rng = np.random.default_rng(5 + device + 2 * weighted)
+    n = 3000
+    a = rng.integers(0, n, 40000); b = rng.integers(0, n, 40000)
+    keep = a != b
+    a, b = a[keep].astype(np.int32), b[keep].astype(np.int32)
+    w = synth.quantise_weights(rng.lognormal(0, 1, a.shape[0])) if weighted else None
+    g = synth.Graph(n=n, u=a, v=b, w=w)
+    h = _load(pkg, g, device)
+    ou, ov, ow, ndup = orc.canonicalize(n, a, b, None if w is None else w.astype(np.float64))
+    gu, gv, gw = pkg.lowd_get_graph(h)
+    assert np.array_equal(_np(gu), ou) and np.array_equal(_np(gv), ov)
+    if weighted:
+        assert np.array_equal(_np(gw).astype(np.float64), ow)
+    else:
+        assert np.all(_np(gw) == 1.0)
+    info = pkg.lowd_get_info(h)
+    assert info["duplicates"] == ndup and info["m"] == ou.shape[0] and info["n"] == n
+    deg = np.bincount(ou, minlength=n) + np.bincount(ov, minlength=n)
+    assert info["max_degree"] == deg.max()
+    pkg.lowd_free(h)
+
+
+def test_load_rejects_bad_input(pkg):
+    g = synth.Graph(n=4, u=np.array([0, 1], np.int32), v=np.array([1, 1], np.int32), w=None)
+    with pytest.raises(pkg.LowdError) as e:
+        _load(pkg, g, False)
+    assert e.value.status == pkg.LOWD_ERR_INVALID_ARG
+    g = synth.Graph(n=4, u=np.array([0, 1], np.int32), v=np.array([1, 4], np.int32), w=None)
+    with pytest.raises(pkg.LowdError) as e:
+        _load(pkg, g, False)
+    assert e.value.status == pkg.LOWD_ERR_INVALID_ARG
+    g = synth.Graph(n=4, u=np.array([0, 1], np.int32), v=np.array([1, 2], np.int32), w=None)
+    for bad in ([1.0, 0.0], [1.0, -2.0], [1.0, np.inf], [np.nan, 1.0]):
+        with pytest.raises(pkg.LowdError) as e:
+            _load(pkg, g, False, w=np.array(bad, np.float32))
+        assert e.value.status == pkg.LOWD_ERR_INVALID_ARG
+    with pytest.raises(pkg.LowdError) as e:
+        _load(pkg, g, False, w=np.array([1.0, 0.1], np.float32))
+    assert e.value.status == pkg.LOWD_ERR_INEXACT_WEIGHTS
+    h = _load(pkg, g, False, w=np.array([1.0, 0.1], np.float32), flags=pkg.LOWD_LOAD_ALLOW_INEXACT)
+    pkg.lowd_free(h)
+
+
+# ----------------------------------------------------------------------------- pruning
+
+def _prune_cases():
+    return [
+        ("chunglu_10k", None),
+        ("cl_small", False), ("cl_small", True),
+        ("planted", False), ("planted", True),
+        ("star", False), ("two_cliques", False), ("empty", False), ("gnp0.3", True),
+    ]
+
+
+def _graph(name, weighted):
+    if name == "chunglu_10k":
+        return synth.workload("chunglu_10k")
+    if name == "cl_small":
+        g = synth.chung_lu(5000, 30000, 2.3, seed=21, block_size=40, block_p=0.5)
+    elif name == "planted":
+        g = synth.planted_background(4000, 4.0, 64, 0.6, seed=9)
+    else:
+        return synth.small_family(name, 40, seed=3, weighted=bool(weighted))
+    if weighted:
+        g.w = synth.quantise_weights(np.random.default_rng(4).lognormal(0, 1, g.m))
+    return g
+
+
+@pytest.mark.parametrize("name,weighted", _prune_cases())
+def test_prune_bit_exact(pkg, orc, name, weighted):
+    g = _graph(name, weighted)
+    h = _load(pkg, g, True)
+    nk, mk, rounds = pkg.lowd_prune(h)
+    wu, _ = orc.weight_units(g.m, g.w)
+    deg = orc.degrees(g.n, g.u, g.v, wu)
+    perm_o = orc.degree_order(deg, g.w is not None)
+    pr = orc.prune(g.n, g.u, g.v, wu, g.w is not None)
+    perm, rr = pkg.lowd_get_prune_info(h)
+    assert np.array_equal(_np(perm), perm_o)
+    assert np.array_equal(_np(rr), pr["removal_round"])
+    assert rounds == pr["rounds"]
+    keep = pr["removal_round"] < 0
+    nh, uh, vh, wh, idmap = orc.compact(g.n, g.u, g.v, g.w, keep)
+    assert (nk, mk) == (nh, uh.shape[0])
+    gu, gv, gw = pkg.lowd_get_graph(h)
+    assert np.array_equal(_np(gu), uh) and np.array_equal(_np(gv), vh)
+    if g.w is not None:
+        assert np.array_equal(_np(gw), wh)
+    info = pkg.lowd_get_info(h)
+    assert info["pruned"] == 1 and info["prune_rounds"] == rounds
+    # call order: pruning twice, or after passes, is refused
+    with pytest.raises(pkg.LowdError) as e:
+        pkg.lowd_prune(h)
+    assert e.value.status == pkg.LOWD_ERR_BAD_STATE
+    pkg.lowd_free(h)
+
+
+# ----------------------------------------------------------------------------- LOWD passes
+
+def _same_order(pkg, orc, g, prune, T, device=True):
+    h = _load(pkg, g, device)
+    if prune:
+        pkg.lowd_prune(h)
+    gu, gv, gw = pkg.lowd_get_graph(h)
+    gu, gv, gw = _np(gu), _np(gv), _np(gw)
+    info = pkg.lowd_get_info(h)
+    pkg.lowd_iterate(h, T)
+    perm, offs = pkg.lowd_get_edge_order(h)
+    perm, offs = _np(perm), _np(offs)
+    o = orc.LowdState(info["n"], gu, gv, None if g.w is None else gw.astype(np.float64))
+    o.iterate(T, order=perm)
+    return h, o, perm, offs, (gu, gv, gw), info
+
+
+@pytest.mark.parametrize("name,prune,T", [
+    ("chunglu_10k", True, 1), ("chunglu_10k", True, 50), ("chunglu_10k", True, 500),
+    ("chunglu_10k", False, 20), ("cl_small", False, 30), ("planted", True, 40),
+])
+def test_same_order_loads(pkg, orc, name, prune, T):
+    g = _graph(name, False if name != "planted" else False)
+    h, o, perm, offs, (gu, gv, gw), info = _same_order(pkg, orc, g, prune, T)
+    # the schedule is a permutation whose classes are matchings
+    assert np.array_equal(np.sort(perm), np.arange(info["m"]))
+    for c in range(offs.shape[0] - 1):
+        cls = perm[offs[c]:offs[c + 1]]
+        ends = np.concatenate([gu[cls], gv[cls]])
+        assert np.unique(ends).shape[0] == ends.shape[0]
+    lg = _np(pkg.lowd_get_loads(h)).astype(np.float64)
+    scale = max(1.0, o.l.max())
+    assert np.max(np.abs(lg - o.l)) <= LOAD_TOL * scale
+    sg = _np(pkg.lowd_get_splits(h)).astype(np.float64)
+    assert np.all(sg >= 0) and np.all(sg <= 1.0)
+    # conservation of the FP32 state: sum of loads equals the number of edges
+    assert abs(lg.sum() - info["m"]) <= 1e-6 * max(1, info["m"])
+    pkg.lowd_free(h)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_same_order_weighted_and_sumsq(pkg, orc, weighted):
+    g = synth.chung_lu(3000, 20000, 2.2, seed=31, block_size=30, block_p=0.5)
+    if weighted:
+        g.w = synth.quantise_weights(np.random.default_rng(8).lognormal(0, 1, g.m))
+    h = _load(pkg, g, True)
+    pkg.lowd_prune(h)
+    gu, gv, gw = (_np(x) for x in pkg.lowd_get_graph(h))
+    info = pkg.lowd_get_info(h)
+    o = orc.LowdState(info["n"], gu, gv, None if g.w is None else gw.astype(np.float64))
+    prev = None
+    for t in range(12):
+        st = pkg.lowd_iterate(h, 5)
+        if t == 0:
+            perm = _np(pkg.lowd_get_edge_order(h)[0])
+        o.iterate(5, order=perm)
+        lg = _np(pkg.lowd_get_loads(h)).astype(np.float64)
+        assert np.max(np.abs(lg - o.l)) <= LOAD_TOL * max(1.0, o.l.max())
+        # sum of squared loads falls monotonically (Sec. III-C), up to FP32 rounding
+        if prev is not None:
+            assert st["sum_load_sq"] <= prev * (1 + 1e-6)
+        prev = st["sum_load_sq"]
+        assert abs(st["sum_load"] - float(gw.astype(np.float64).sum())) <= 1e-6 * st["sum_load"]
+    pkg.lowd_free(h)
+
+
+# ----------------------------------------------------------------------------- extraction
+
+@pytest.mark.parametrize("name,T", [("chunglu_10k", 0), ("chunglu_10k", 3), ("chunglu_10k", 40),
+                                    ("cl_small", 25), ("two_cliques", 5)])
+def test_extract_bit_exact_on_gpu_loads(pkg, orc, name, T):
+    g = _graph(name, False)
+    h = _load(pkg, g, True)
+    if name != "two_cliques":
+        pkg.lowd_prune(h)
+    if T:
+        pkg.lowd_iterate(h, T)
+    gu, gv, gw = (_np(x) for x in pkg.lowd_get_graph(h))
+    info = pkg.lowd_get_info(h)
+    lg = _np(pkg.lowd_get_loads(h))
+    S, rho, loads = pkg.lowd_extract(h)
+    wu, scale = orc.weight_units(gu.shape[0], None)
+    So, Wo = orc.extract(info["n"], gu, gv, wu, lg.astype(np.float64))
+    # map the oracle's current ids to original ids
+    if info["pruned"]:
+        _, rr = pkg.lowd_get_prune_info(h)
+        idmap = np.nonzero(_np(rr) < 0)[0]
+        So = idmap[So]
+    assert np.array_equal(_np(S), So)
+    assert rho == Wo / scale / So.shape[0]
+    full = _np(loads)
+    assert full.shape[0] == g.n
+    pkg.lowd_free(h)
+
+
+# ----------------------------------------------------------------------------- convergence
+
+@pytest.mark.parametrize("name,weighted,T", [("chunglu_10k", False, 2000), ("cl_small", True, 3000),
+                                             ("planted", False, 400)])
+def test_converged_loads_and_densest_set(pkg, orc, name, weighted, T):
+    g = _graph(name, weighted if name != "chunglu_10k" else None)
+    h = _load(pkg, g, True)
+    pkg.lowd_prune(h)
+    st = pkg.lowd_iterate(h, T, check_every=100, rel_tol=1e-9)
+    S, rho, loads = pkg.lowd_extract(h)
+    wu, scale = orc.weight_units(g.m, g.w)
+    rho_star, B1 = orc.densest_flow(g.n, g.u, g.v, wu)
+    assert abs(rho - float(rho_star) / scale) <= 1e-9 * float(rho_star) / scale
+    assert np.array_equal(_np(S), np.nonzero(B1)[0])
+    # converged loads against the exact decomposition of the pruned graph
+    gu, gv, gw = (_np(x) for x in pkg.lowd_get_graph(h))
+    info = pkg.lowd_get_info(h)
+    whu, _ = orc.weight_units(gu.shape[0], None if g.w is None else gw)
+    lstar, shell, lam = orc.ldd_loads(info["n"], gu, gv, whu, scale)
+    lg = _np(pkg.lowd_get_loads(h)).astype(np.float64)
+    assert np.max(np.abs(lg - lstar)) <= 1e-4 * lstar.max()
+    # the loads reported in original numbering: zero for pruned nodes
+    _, rr = pkg.lowd_get_prune_info(h)
+    full = _np(loads)
+    assert np.all(full[_np(rr) >= 0] == 0)
+    assert np.array_equal(full[_np(rr) < 0], lg.astype(np.float32))
+    pkg.lowd_free(h)
+
+
+# ----------------------------------------------------------------------------- edge cases and state
+
+def test_edge_cases(pkg, orc):
+    # no edges: nothing pruned, S* = V, rho = 0
+    g = synth.Graph(n=5, u=np.zeros(0, np.int32), v=np.zeros(0, np.int32), w=None)
+    for prune in (False, True):
+        h = _load(pkg, g, prune)
+        if prune:
+            assert pkg.lowd_prune(h) == (5, 0, 0)
+        pkg.lowd_iterate(h, 3)
+        S, rho, loads = pkg.lowd_extract(h)
+        assert _np(S).tolist() == [0, 1, 2, 3, 4] and rho == 0.0
+        pkg.lowd_free(h)
+    # one node
+    g = synth.Graph(n=1, u=np.zeros(0, np.int32), v=np.zeros(0, np.int32), w=None)
+    h = _load(pkg, g, True)
+    pkg.lowd_iterate(h, 2)
+    S, rho, _ = pkg.lowd_extract(h)
+    assert _np(S).tolist() == [0] and rho == 0.0
+    pkg.lowd_free(h)
+    # single edge, both orientations given: one edge, rho = 1/2
+    g = synth.Graph(n=3, u=np.array([2, 1], np.int32), v=np.array([1, 2], np.int32), w=None)
+    h = _load(pkg, g, False)
+    assert pkg.lowd_get_info(h)["m"] == 1
+    pkg.lowd_iterate(h, 4)
+    S, rho, _ = pkg.lowd_extract(h)
+    assert _np(S).tolist() == [1, 2] and rho == 0.5
+    pkg.lowd_free(h)
+    # extraction before any pass uses the equal-split loads (degree / 2)
+    g = synth.chung_lu(500, 2000, 2.1, seed=1)
+    h = _load(pkg, g, True)
+    lg = _np(pkg.lowd_get_loads(h))
+    deg = np.bincount(g.u, minlength=g.n) + np.bincount(g.v, minlength=g.n)
+    assert np.array_equal(lg, (deg / 2).astype(np.float32))
+    pkg.lowd_free(h)
+
+
+def test_too_large_for_shared_memory_sweep_is_an_error(pkg):
+    g = synth.Graph(n=60000, u=np.arange(0, 59998, 2, dtype=np.int32),
+                    v=np.arange(1, 59999, 2, dtype=np.int32), w=None)
+    h = _load(pkg, g, True)
+    with pytest.raises(pkg.LowdError) as e:
+        pkg.lowd_iterate(h, 1)
+    assert e.value.status == pkg.LOWD_ERR_TOO_LARGE
+    pkg.lowd_free(h)
+
+
+def test_splits_checkpoint_resume(pkg, orc):
+    g = synth.workload("chunglu_10k")
+    h1 = _load(pkg, g, True)
+    pkg.lowd_prune(h1)
+    pkg.lowd_iterate(h1, 30)
+    s30 = pkg.lowd_get_splits(h1)
+    pkg.lowd_iterate(h1, 30)
+    l60 = _np(pkg.lowd_get_loads(h1))
+    h2 = _load(pkg, g, True)
+    pkg.lowd_prune(h2)
+    pkg.lowd_set_splits(h2, s30)
+    pkg.lowd_iterate(h2, 30)
+    l60b = _np(pkg.lowd_get_loads(h2))
+    assert np.max(np.abs(l60 - l60b)) <= 1e-5 * l60.max()
+    pkg.lowd_free(h1); pkg.lowd_free(h2)
