@@ -267,6 +267,23 @@ def main():
         sweep_s = max(durs[T] - durs[0], 1e-9)
         pkg.lowd_free(h)
 
+        # per-stage device time of one step (events between the calls)
+        stages = {}
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        evs[0].record(stream)
+        h = pkg.lowd_load_graph(g.n, du, dv, dw, stream=stream)
+        evs[1].record(stream)
+        pkg.lowd_prune(h)
+        evs[2].record(stream)
+        pkg.lowd_iterate(h, T)
+        evs[3].record(stream)
+        pkg.lowd_extract(h, want_loads=False)
+        evs[4].record(stream)
+        evs[4].synchronize()
+        for i, nm in enumerate(("load", "prune", "iterate", "extract")):
+            stages[nm] = evs[i].elapsed_time(evs[i + 1])
+        pkg.lowd_free(h)
+
         # end to end through the C ABI with pinned host buffers (copies inside the timing)
         hu = torch.from_numpy(g.u).pin_memory().numpy()
         hv = torch.from_numpy(g.v).pin_memory().numpy()
@@ -309,6 +326,7 @@ def main():
                      "launch_ms": sweep_s * 1e3, "bytes_per_update": BYTES_PER_UPDATE},
         "e2e": {"value": m_H * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+        "stages_ms": stages,
         "gpu_launches": int(launches),
         "gpu_launches_per_step": int(launches // max(args.steps, 1)),
         "clocks": ck,

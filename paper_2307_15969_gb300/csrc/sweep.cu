@@ -227,6 +227,111 @@ k_sweep_cta(int32_t n, int32_t C, const int32_t* __restrict__ coff,
     for (int i = tid; i < n; i += kCtaThreads) l[i] = L[i];
 }
 
+
+// Deep-pipelined form of the same sweep.  The classes of all passes form one stream
+// q = 0, 1, ... (class q mod C); each thread owns position `tid` of every class and keeps
+// the edge data of the next kRing classes of the stream in a register ring, so a global
+// load is issued kRing classes (several hundred cycles) before its use.  The class
+// offsets live in shared memory when they fit next to the loads.  The load for class
+// q + kRing is issued after class q is updated, so when a class comes round again in the
+// next pass (C >= kRing) its split was already written by the same thread.  Positions
+// past blockDim.x in a class are updated directly from global memory.
+constexpr int kRing = 8;
+
+template <bool WEIGHTED>
+__device__ __forceinline__ void ring_issue(int32_t cls, bool ok, const int32_t* CO, int tid,
+                                           const uint32_t* __restrict__ cuv, const float* __restrict__ cw,
+                                           const float* __restrict__ cs, int32_t& si, uint32_t& suv,
+                                           float& ss, float& sw) {
+    si = -1;
+    if (ok) {
+        int32_t i = CO[cls] + tid;
+        if (i < CO[cls + 1]) {
+            si = i;
+            suv = __ldg(cuv + i);
+            ss = __ldcg(cs + i);
+            if (WEIGHTED) sw = __ldg(cw + i);
+        }
+    }
+}
+
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(kCtaThreads, 1)
+k_sweep_ring(int32_t n, int32_t C, const int32_t* __restrict__ coff, int32_t co_smem,
+             const uint32_t* __restrict__ cuv, const float* __restrict__ cw,
+             float* __restrict__ cs, float* __restrict__ l, int32_t passes) {
+    extern __shared__ float L[];
+    int32_t* COs = reinterpret_cast<int32_t*>(L + n);
+    const int tid = threadIdx.x;
+    const int B = blockDim.x;
+    for (int i = tid; i < n; i += B) L[i] = l[i];
+    if (co_smem)
+        for (int i = tid; i <= C; i += B) COs[i] = coff[i];
+    __syncthreads();
+    const int32_t* CO = co_smem ? COs : coff;
+    const int64_t Q = (int64_t)C * passes;
+    int32_t si[kRing];
+    uint32_t suv[kRing];
+    float ss[kRing], sw[kRing];
+    int32_t c_issue = 0;
+    int64_t q_issue = 0;
+#pragma unroll
+    for (int j = 0; j < kRing; ++j) {
+        ring_issue<WEIGHTED>(c_issue, q_issue < Q, CO, tid, cuv, cw, cs, si[j], suv[j], ss[j], sw[j]);
+        c_issue = (c_issue + 1 == C) ? 0 : c_issue + 1;
+        ++q_issue;
+    }
+    int32_t c = 0;
+    for (int64_t q0 = 0; q0 < Q; q0 += kRing) {
+#pragma unroll
+        for (int j = 0; j < kRing; ++j) {
+            if (q0 + j < Q) {
+                if (si[j] >= 0) {
+                    EdgeReg r;
+                    r.a = (int32_t)(suv[j] & 0xffffu);
+                    r.b = (int32_t)(suv[j] >> 16);
+                    r.s = ss[j];
+                    r.w = WEIGHTED ? sw[j] : 1.0f;
+                    lowd_edge(L, r);
+                    __stcg(cs + si[j], r.s);
+                }
+                const int32_t end = CO[c + 1];
+                for (int32_t i = CO[c] + B + tid; i < end; i += B) {
+                    EdgeReg r = load_edge<true, WEIGHTED>(i, cuv, nullptr, nullptr, cw, cs);
+                    lowd_edge(L, r);
+                    cs[i] = r.s;
+                }
+                ring_issue<WEIGHTED>(c_issue, q_issue < Q, CO, tid, cuv, cw, cs, si[j], suv[j], ss[j], sw[j]);
+                c_issue = (c_issue + 1 == C) ? 0 : c_issue + 1;
+                ++q_issue;
+                c = (c + 1 == C) ? 0 : c + 1;
+                __syncthreads();
+            }
+        }
+    }
+    for (int i = tid; i < n; i += B) l[i] = L[i];
+}
+
+template <bool WEIGHTED>
+cudaError_t launch_ring(lowd_ctx* h, int32_t passes) {
+    const size_t lbytes = sizeof(float) * (size_t)h->n;
+    const size_t cbytes = sizeof(int32_t) * ((size_t)h->C + 1);
+    const size_t budget = 227 * 1024;
+    const int co_smem = lbytes + cbytes <= budget ? 1 : 0;
+    const size_t smem = lbytes + (co_smem ? cbytes : 0);
+    int32_t maxc = 0;
+    for (int32_t c = 0; c < h->C; ++c) maxc = max(maxc, h->coff_h[c + 1] - h->coff_h[c]);
+    int threads = ((maxc + 31) / 32) * 32;
+    if (threads < 128) threads = 128;
+    if (threads > kCtaThreads) threads = kCtaThreads;
+    auto kern = k_sweep_ring<WEIGHTED>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    LOWD_LAUNCH(kern, 1, threads, smem, h->st, h->n, h->C, h->coff, co_smem, h->cuv, h->cw, h->cs, h->l,
+                passes);
+    return cudaGetLastError();
+}
+
 template <bool PACKED, bool WEIGHTED>
 cudaError_t launch_cta(lowd_ctx* h, int32_t passes) {
     size_t smem = sizeof(float) * (size_t)(h->n > 0 ? h->n : 1);
@@ -241,6 +346,7 @@ cudaError_t run_passes(lowd_ctx* h, int32_t passes) {
     if (passes <= 0 || h->m == 0) return cudaSuccess;
     const bool packed = h->cuv != nullptr;
     const bool weighted = h->cw != nullptr;
+    if (packed && h->C >= kRing) return weighted ? launch_ring<true>(h, passes) : launch_ring<false>(h, passes);
     if (packed && weighted) return launch_cta<true, true>(h, passes);
     if (packed) return launch_cta<true, false>(h, passes);
     if (weighted) return launch_cta<false, true>(h, passes);
