@@ -26,7 +26,7 @@ lowd_status to_caller(lowd_ctx* h, T* dst, const T* src_dev, size_t n) {
 void free_all(lowd_ctx* h) {
     dfree(&h->u); dfree(&h->v); dfree(&h->w); dfree(&h->wu); dfree(&h->map);
     dfree(&h->sort_perm); dfree(&h->removal_round);
-    dfree(&h->perm); dfree(&h->coff); dfree(&h->cuv); dfree(&h->cu); dfree(&h->cv);
+    dfree(&h->perm); dfree(&h->coff); dfree(&h->coff_real); dfree(&h->cuv);
     dfree(&h->cw); dfree(&h->cs); dfree(&h->l);
     dfree(&h->tmp); h->tmp_cap = 0;
     dfree(&h->d_stats); dfree(&h->d_i64); dfree(&h->d_i32);
@@ -355,8 +355,16 @@ lowd_status lowd_get_prune_info(lowd_handle h, int32_t* sort_perm, int32_t* remo
 lowd_status lowd_get_edge_order(lowd_handle h, int32_t* perm, int32_t* class_offsets, int32_t* classes) {
     LOWD_TRY(check_handle(h));
     if (!h->inited) return LOWD_ERR_BAD_STATE;
-    LOWD_TRY(to_caller(h, perm, h->perm, (size_t)h->m));
-    LOWD_TRY(to_caller(h, class_offsets, h->coff, (size_t)h->C + 1));
+    if (perm) {
+        int32_t* d = nullptr;
+        LOWD_TRY(dalloc(h, &d, h->m));
+        lowd_status r = lowd_sweep_edge_order(h, d);
+        if (r == LOWD_OK) r = to_caller(h, perm, d, (size_t)h->m);
+        cudaStreamSynchronize(h->st);
+        dfree(&d);
+        LOWD_TRY(r);
+    }
+    LOWD_TRY(to_caller(h, class_offsets, h->coff_real, (size_t)h->C + 1));
     if (classes) *classes = h->C;
     return LOWD_OK;
 }

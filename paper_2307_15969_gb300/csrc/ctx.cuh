@@ -47,17 +47,15 @@ struct lowd_ctx {
     int32_t iters = 0;
     int sched = 0;             // 1 one-CTA shared memory, 2 grid matchings
     int32_t C = 0;             // number of classes
-    int32_t* perm = nullptr;   // [m] class-major position -> canonical edge id
-    int32_t* coff = nullptr;   // [C+1] device class offsets
-    int32_t* coff_h = nullptr; // [C+1] host copy
-    uint32_t* cuv = nullptr;   // [m] packed (lo | hi << 16) when n <= 65536
-    int32_t* cu = nullptr;     // [m] endpoints in class-major order (n > 65536)
-    int32_t* cv = nullptr;
-    float* cw = nullptr;       // [m] weights in class-major order (weighted only)
-    float* cs = nullptr;       // [m] splits f_e(lo) in class-major order
-    float* l = nullptr;        // [n] loads
-    // grid schedule: launch plan built on the host from coff_h
-    int32_t n_big = 0;         // classes [0, n_big) run as grid launches
+    int64_t m_pad = 0;         // class-major length, each class padded to a multiple of 4
+    int32_t* perm = nullptr;   // [m_pad] class-major position -> canonical edge id, -1 = padding
+    int32_t* coff = nullptr;   // [C+1] padded class offsets (multiples of 4)
+    int32_t* coff_real = nullptr; // [C+1] class offsets without padding
+    int32_t* coff_h = nullptr; // [C+1] host copy of coff
+    uint32_t* cuv = nullptr;   // [m_pad] packed ends (lo | hi << 16); padding: (n | n << 16)
+    float* cw = nullptr;       // [m_pad] weights (weighted only); padding 0
+    float* cs = nullptr;       // [m_pad] splits f_e(lo); padding 0
+    float* l = nullptr;        // [n + 1] loads; slot n is the padding sentinel
 
     // scratch
     void* tmp = nullptr;
@@ -129,6 +127,7 @@ lowd_status lowd_sweep_run(lowd_ctx* h, int32_t k, const lowd_options* opt, lowd
 lowd_status lowd_sweep_rederive(lowd_ctx* h, double* stats3);
 lowd_status lowd_sweep_splits_canonical(lowd_ctx* h, float* out_dev);
 lowd_status lowd_sweep_load_canonical(lowd_ctx* h, const float* splits_dev);
+lowd_status lowd_sweep_edge_order(lowd_ctx* h, int32_t* out_dev);
 
 // extract.cu
 lowd_status lowd_extract_best(lowd_ctx* h, const float* loads_dev, int32_t* S_dev_current,

@@ -28,8 +28,6 @@ using namespace lowd;
 namespace {
 
 constexpr int kT = 256;
-constexpr int kCtaThreads = 1024;
-constexpr int kPre = 2;  // edges per thread prefetched for the next class
 
 inline unsigned grid_for(int64_t n) {
     int64_t b = (n + kT - 1) / kT;
@@ -65,37 +63,64 @@ __global__ void k_class_offsets(const int32_t* __restrict__ head, const int32_t*
     if (blockIdx.x == 0 && threadIdx.x == 0) coff[C] = (int32_t)m;
 }
 
-// Gather the class-major streams: endpoints (packed or not), weights, initial splits.
-__global__ void k_gather_streams(const int32_t* __restrict__ perm, int64_t m,
-                                 const int32_t* __restrict__ u, const int32_t* __restrict__ v,
-                                 const float* __restrict__ w, const float* __restrict__ s_init,
-                                 uint32_t* __restrict__ cuv, int32_t* __restrict__ cu,
-                                 int32_t* __restrict__ cv, float* __restrict__ cw,
-                                 float* __restrict__ cs) {
+// Class segments padded to a multiple of 4 edges: pcnt[c] = roundup4(size of class c).
+__global__ void k_pad_sizes(const int32_t* __restrict__ coff_real, int32_t C, int32_t* __restrict__ pcnt) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (int64_t)gridDim.x * blockDim.x)
+        pcnt[c] = (coff_real[c + 1] - coff_real[c] + 3) & ~3;
+}
+
+__global__ void k_fill_perm(int32_t* __restrict__ perm_pad, int64_t m_pad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_pad;
+         i += (int64_t)gridDim.x * blockDim.x)
+        perm_pad[i] = -1;
+}
+
+// Real position i (class-major, unpadded) -> padded position.
+__global__ void k_scatter_padded(const int32_t* __restrict__ perm, const int32_t* __restrict__ head,
+                                 const int32_t* __restrict__ hpos, const int32_t* __restrict__ coff_real,
+                                 const int32_t* __restrict__ coff_pad, int64_t m,
+                                 int32_t* __restrict__ perm_pad) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t e = perm[i];
-        int32_t a = u[e], b = v[e];
-        if (cuv) cuv[i] = (uint32_t)a | ((uint32_t)b << 16);
-        else { cu[i] = a; cv[i] = b; }
-        float we = w ? w[e] : 1.0f;
-        if (cw) cw[i] = we;
-        float s = s_init ? fminf(fmaxf(s_init[e], 0.0f), we) : we * 0.5f;  // Alg. 1: w_e / 2
-        cs[i] = s;
+        int32_t c = hpos[i] + head[i] - 1;
+        perm_pad[coff_pad[c] + (i - coff_real[c])] = perm[i];
     }
 }
 
-// FP64 loads from the splits: l_x = sum over edges at x of f_e(x).
-__global__ void k_rederive(int64_t m, const uint32_t* __restrict__ cuv, const int32_t* __restrict__ cu,
-                           const int32_t* __restrict__ cv, const float* __restrict__ cw,
-                           const float* __restrict__ cs, double* __restrict__ L64) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+// Class-major streams over the padded positions: packed ends, weights, initial splits;
+// padding edges join the sentinel node n to itself with s = w = 0 (a no-op update).
+__global__ void k_gather_streams(const int32_t* __restrict__ perm_pad, int64_t m_pad, int32_t n,
+                                 const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                                 const float* __restrict__ w, const float* __restrict__ s_init,
+                                 uint32_t* __restrict__ cuv, float* __restrict__ cw,
+                                 float* __restrict__ cs) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_pad;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t a, b;
-        if (cuv) { uint32_t p = cuv[i]; a = (int32_t)(p & 0xffffu); b = (int32_t)(p >> 16); }
-        else { a = cu[i]; b = cv[i]; }
-        double s = (double)cs[i];
-        double w = cw ? (double)cw[i] : 1.0;
+        const int32_t e = perm_pad[i];
+        if (e < 0) {
+            cuv[i] = (uint32_t)n | ((uint32_t)n << 16);
+            if (cw) cw[i] = 0.0f;
+            cs[i] = 0.0f;
+            continue;
+        }
+        cuv[i] = (uint32_t)u[e] | ((uint32_t)v[e] << 16);
+        const float we = w ? w[e] : 1.0f;
+        if (cw) cw[i] = we;
+        cs[i] = s_init ? fminf(fmaxf(s_init[e], 0.0f), we) : we * 0.5f;  // Alg. 1: w_e / 2
+    }
+}
+
+// FP64 loads from the splits: l_x = sum over edges at x of f_e(x) (padding skipped).
+__global__ void k_rederive(int64_t m_pad, const uint32_t* __restrict__ cuv, const float* __restrict__ cw,
+                           const float* __restrict__ cs, double* __restrict__ L64) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_pad;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = cuv[i];
+        const int32_t a = (int32_t)(p & 0xffffu), b = (int32_t)(p >> 16);
+        if (a == b) continue;
+        const double s = (double)cs[i];
+        const double w = cw ? (double)cw[i] : 1.0;
         atomicAdd(&L64[a], s);
         atomicAdd(&L64[b], w - s);
     }
@@ -128,156 +153,143 @@ __global__ void k_load_stats(const double* __restrict__ L64, int32_t n, float* _
     }
 }
 
-__global__ void k_splits_from_canonical(const int32_t* __restrict__ perm, int64_t m,
+__global__ void k_splits_from_canonical(const int32_t* __restrict__ perm_pad, int64_t m_pad,
                                         const float* __restrict__ in, float* __restrict__ cs) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x)
-        cs[i] = in[perm[i]];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_pad;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = perm_pad[i];
+        if (e >= 0) cs[i] = in[e];
+    }
 }
 
-__global__ void k_splits_to_canonical(const int32_t* __restrict__ perm, int64_t m,
+__global__ void k_splits_to_canonical(const int32_t* __restrict__ perm_pad, int64_t m_pad,
                                       const float* __restrict__ cs, float* __restrict__ out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[perm[i]] = cs[i];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_pad;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = perm_pad[i];
+        if (e >= 0) out[e] = cs[i];
+    }
 }
 
-struct EdgeReg {
-    int32_t a, b;
-    float s, w;
+__global__ void k_real_flags(const int32_t* __restrict__ perm_pad, int64_t m_pad, int32_t* __restrict__ f) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_pad;
+         i += (int64_t)gridDim.x * blockDim.x)
+        f[i] = perm_pad[i] >= 0 ? 1 : 0;
+}
+
+__global__ void k_compact_perm(const int32_t* __restrict__ perm_pad, const int32_t* __restrict__ f,
+                               const int32_t* __restrict__ pos, int64_t m_pad, int32_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_pad;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (f[i]) out[pos[i]] = perm_pad[i];
+}
+
+// One LOWD update (Algorithm 1's loop body) on e = (a, b) with f_e(a) = s, f_e(b) = w - s,
+// written without branches: dd is the weight moved from a to b (negative: from b to a).
+// |l_a - l_b| * 0.5 is exactly the paper's (l_u - l_v)/2 or (l_v - l_u)/2.
+struct EdgeVal {
+    float la, lb, s, w;
 };
 
-template <bool PACKED, bool WEIGHTED>
-__device__ __forceinline__ EdgeReg load_edge(int64_t i, const uint32_t* __restrict__ cuv,
-                                             const int32_t* __restrict__ cu, const int32_t* __restrict__ cv,
-                                             const float* __restrict__ cw, const float* __restrict__ cs) {
-    EdgeReg r;
-    if (PACKED) { uint32_t p = __ldg(cuv + i); r.a = (int32_t)(p & 0xffffu); r.b = (int32_t)(p >> 16); }
-    else { r.a = __ldg(cu + i); r.b = __ldg(cv + i); }
-    r.w = WEIGHTED ? __ldg(cw + i) : 1.0f;
-    r.s = cs[i];
+__device__ __forceinline__ float lowd_transfer(EdgeVal& e) {
+    const float diff = e.la - e.lb;
+    const bool gt = diff > 0.0f;
+    const float cap = gt ? e.s : (e.w - e.s);
+    const float d = fminf(fabsf(diff) * 0.5f, cap);
+    const float dd = gt ? d : -d;
+    e.la -= dd;
+    e.lb += dd;
+    return fminf(e.s - dd, e.w);
+}
+
+__device__ __forceinline__ uint32_t end_a(uint32_t uv) { return uv & 0xffffu; }
+__device__ __forceinline__ uint32_t end_b(uint32_t uv) { return uv >> 16; }
+
+// Four edges of one class: gather the 8 loads first (the ends are distinct inside a
+// class, so no update can see another's write), update, scatter.
+template <bool WEIGHTED>
+__device__ __forceinline__ float4 update4(float* L, const uint4& uv, const float4& s, const float4& w) {
+    EdgeVal e0{L[end_a(uv.x)], L[end_b(uv.x)], s.x, WEIGHTED ? w.x : 1.0f};
+    EdgeVal e1{L[end_a(uv.y)], L[end_b(uv.y)], s.y, WEIGHTED ? w.y : 1.0f};
+    EdgeVal e2{L[end_a(uv.z)], L[end_b(uv.z)], s.z, WEIGHTED ? w.z : 1.0f};
+    EdgeVal e3{L[end_a(uv.w)], L[end_b(uv.w)], s.w, WEIGHTED ? w.w : 1.0f};
+    float4 r;
+    r.x = lowd_transfer(e0);
+    r.y = lowd_transfer(e1);
+    r.z = lowd_transfer(e2);
+    r.w = lowd_transfer(e3);
+    L[end_a(uv.x)] = e0.la; L[end_b(uv.x)] = e0.lb;
+    L[end_a(uv.y)] = e1.la; L[end_b(uv.y)] = e1.lb;
+    L[end_a(uv.z)] = e2.la; L[end_b(uv.z)] = e2.lb;
+    L[end_a(uv.w)] = e3.la; L[end_b(uv.w)] = e3.lb;
     return r;
 }
 
-// The LOWD edge update of Algorithm 1 on e = (a, b) with f_e(a) = s, f_e(b) = w - s.
-__device__ __forceinline__ void lowd_edge(float* L, EdgeReg& r) {
-    float la = L[r.a], lb = L[r.b];
-    float d;
-    if (la > lb) {
-        d = fminf((la - lb) * 0.5f, r.s);
-        la -= d; lb += d;
-        r.s -= d;
-    } else {
-        d = fminf((lb - la) * 0.5f, r.w - r.s);
-        la += d; lb -= d;
-        r.s = fminf(r.s + d, r.w);
-    }
-    L[r.a] = la; L[r.b] = lb;
-}
-
-template <bool PACKED, bool WEIGHTED>
-__global__ void __launch_bounds__(kCtaThreads, 1)
-k_sweep_cta(int32_t n, int32_t C, const int32_t* __restrict__ coff,
-            const uint32_t* __restrict__ cuv, const int32_t* __restrict__ cu,
-            const int32_t* __restrict__ cv, const float* __restrict__ cw,
-            float* __restrict__ cs, float* __restrict__ l, int32_t passes) {
-    extern __shared__ float L[];
-    const int tid = threadIdx.x;
-    for (int i = tid; i < n; i += kCtaThreads) L[i] = l[i];
-    __syncthreads();
-    for (int32_t t = 0; t < passes; ++t) {
-        int32_t beg = __ldg(coff);
-        int32_t end = C > 0 ? __ldg(coff + 1) : beg;
-        // registers for the current class
-        EdgeReg cur[kPre];
-#pragma unroll
-        for (int k = 0; k < kPre; ++k) {
-            int64_t i = (int64_t)beg + tid + (int64_t)k * kCtaThreads;
-            if (i < end) cur[k] = load_edge<PACKED, WEIGHTED>(i, cuv, cu, cv, cw, cs);
-        }
-        for (int32_t c = 0; c < C; ++c) {
-            // prefetch the next class
-            int32_t nb = end, ne = (c + 2 <= C) ? __ldg(coff + c + 2) : end;
-            EdgeReg nxt[kPre];
-#pragma unroll
-            for (int k = 0; k < kPre; ++k) {
-                int64_t i = (int64_t)nb + tid + (int64_t)k * kCtaThreads;
-                if (c + 1 < C && i < ne) nxt[k] = load_edge<PACKED, WEIGHTED>(i, cuv, cu, cv, cw, cs);
-            }
-#pragma unroll
-            for (int k = 0; k < kPre; ++k) {
-                int64_t i = (int64_t)beg + tid + (int64_t)k * kCtaThreads;
-                if (i < end) {
-                    lowd_edge(L, cur[k]);
-                    cs[i] = cur[k].s;
-                }
-            }
-            // classes larger than the prefetch window
-            for (int64_t i = (int64_t)beg + tid + (int64_t)kPre * kCtaThreads; i < end; i += kCtaThreads) {
-                EdgeReg r = load_edge<PACKED, WEIGHTED>(i, cuv, cu, cv, cw, cs);
-                lowd_edge(L, r);
-                cs[i] = r.s;
-            }
-            __syncthreads();
-            beg = nb; end = ne;
-#pragma unroll
-            for (int k = 0; k < kPre; ++k) cur[k] = nxt[k];
-        }
-    }
-    for (int i = tid; i < n; i += kCtaThreads) l[i] = L[i];
-}
-
-
-// Deep-pipelined form of the same sweep.  The classes of all passes form one stream
-// q = 0, 1, ... (class q mod C); each thread owns position `tid` of every class and keeps
-// the edge data of the next kRing classes of the stream in a register ring, so a global
-// load is issued kRing classes (several hundred cycles) before its use.  The class
-// offsets live in shared memory when they fit next to the loads.  The load for class
-// q + kRing is issued after class q is updated, so when a class comes round again in the
-// next pass (C >= kRing) its split was already written by the same thread.  Positions
-// past blockDim.x in a class are updated directly from global memory.
-constexpr int kRing = 8;
+// The sweep.  One CTA; node loads (plus a sentinel slot n used by padding edges) in
+// shared memory for all passes; class offsets in shared memory when they fit.  Each
+// class segment is padded to a multiple of 4 edges with sentinel edges (both ends = n,
+// a no-op), so thread t owns the 16-byte vector t of every class.  The classes of all
+// passes form one stream q = 0, 1, ... (class q mod C); every thread keeps the vectors
+// of the next kRing classes in a register ring, loading class q + kRing right after
+// updating class q.  When a class comes round again in the next pass its splits were
+// written by the same thread (this needs C >= kRing; smaller schedules use the simple
+// kernel).  Vectors beyond blockDim.x of a class are updated straight from memory.
+constexpr int kRingU = 8;  // ring depth, unit weights
+constexpr int kRingW = 6;  // ring depth, weighted (one more vector per slot)
+constexpr int kVecThreads = 512;
 
 template <bool WEIGHTED>
 __device__ __forceinline__ void ring_issue(int32_t cls, bool ok, const int32_t* CO, int tid,
-                                           const uint32_t* __restrict__ cuv, const float* __restrict__ cw,
-                                           const float* __restrict__ cs, int32_t& si, uint32_t& suv,
-                                           float& ss, float& sw) {
-    si = -1;
+                                           const uint4* __restrict__ cuv, const float4* __restrict__ cw,
+                                           const float4* __restrict__ cs, int32_t& vi, uint4& ruv,
+                                           float4& rs, float4& rw) {
+    vi = -1;
     if (ok) {
-        int32_t i = CO[cls] + tid;
-        if (i < CO[cls + 1]) {
-            si = i;
-            suv = __ldg(cuv + i);
-            ss = __ldcg(cs + i);
-            if (WEIGHTED) sw = __ldg(cw + i);
+        const int32_t i = (CO[cls] >> 2) + tid;
+        if (i < (CO[cls + 1] >> 2)) {
+            vi = i;
+            ruv = __ldg(cuv + i);
+            rs = __ldcg(cs + i);
+            if (WEIGHTED) rw = __ldg(cw + i);
         }
     }
 }
 
 template <bool WEIGHTED>
-__global__ void __launch_bounds__(kCtaThreads, 1)
-k_sweep_ring(int32_t n, int32_t C, const int32_t* __restrict__ coff, int32_t co_smem,
-             const uint32_t* __restrict__ cuv, const float* __restrict__ cw,
-             float* __restrict__ cs, float* __restrict__ l, int32_t passes) {
+__device__ __forceinline__ void class_overflow(float* L, int32_t cls, const int32_t* CO, int tid, int B,
+                                               const uint4* __restrict__ cuv, const float4* __restrict__ cw,
+                                               float4* __restrict__ cs) {
+    const int32_t e4 = CO[cls + 1] >> 2;
+    for (int32_t i = (CO[cls] >> 2) + B + tid; i < e4; i += B) {
+        float4 w4 = WEIGHTED ? __ldg(cw + i) : float4{1.f, 1.f, 1.f, 1.f};
+        float4 r = update4<WEIGHTED>(L, __ldg(cuv + i), __ldcg(cs + i), w4);
+        __stcg(cs + i, r);
+    }
+}
+
+template <bool WEIGHTED, int kRing>
+__global__ void __launch_bounds__(kVecThreads, 1)
+k_sweep_vec(int32_t n, int32_t C, const int32_t* __restrict__ coff, int32_t co_smem,
+            const uint4* __restrict__ cuv, const float4* __restrict__ cw, float4* __restrict__ cs,
+            float* __restrict__ l, int32_t passes) {
     extern __shared__ float L[];
-    int32_t* COs = reinterpret_cast<int32_t*>(L + n);
+    int32_t* COs = reinterpret_cast<int32_t*>(L + n + 1);
     const int tid = threadIdx.x;
     const int B = blockDim.x;
-    for (int i = tid; i < n; i += B) L[i] = l[i];
+    for (int i = tid; i <= n; i += B) L[i] = i < n ? l[i] : 0.0f;
     if (co_smem)
         for (int i = tid; i <= C; i += B) COs[i] = coff[i];
     __syncthreads();
     const int32_t* CO = co_smem ? COs : coff;
     const int64_t Q = (int64_t)C * passes;
-    int32_t si[kRing];
-    uint32_t suv[kRing];
-    float ss[kRing], sw[kRing];
+    int32_t vi[kRing];
+    uint4 ruv[kRing];
+    float4 rs[kRing], rw[kRing];
     int32_t c_issue = 0;
     int64_t q_issue = 0;
 #pragma unroll
     for (int j = 0; j < kRing; ++j) {
-        ring_issue<WEIGHTED>(c_issue, q_issue < Q, CO, tid, cuv, cw, cs, si[j], suv[j], ss[j], sw[j]);
+        ring_issue<WEIGHTED>(c_issue, q_issue < Q, CO, tid, cuv, cw, cs, vi[j], ruv[j], rs[j], rw[j]);
         c_issue = (c_issue + 1 == C) ? 0 : c_issue + 1;
         ++q_issue;
     }
@@ -286,22 +298,9 @@ k_sweep_ring(int32_t n, int32_t C, const int32_t* __restrict__ coff, int32_t co_
 #pragma unroll
         for (int j = 0; j < kRing; ++j) {
             if (q0 + j < Q) {
-                if (si[j] >= 0) {
-                    EdgeReg r;
-                    r.a = (int32_t)(suv[j] & 0xffffu);
-                    r.b = (int32_t)(suv[j] >> 16);
-                    r.s = ss[j];
-                    r.w = WEIGHTED ? sw[j] : 1.0f;
-                    lowd_edge(L, r);
-                    __stcg(cs + si[j], r.s);
-                }
-                const int32_t end = CO[c + 1];
-                for (int32_t i = CO[c] + B + tid; i < end; i += B) {
-                    EdgeReg r = load_edge<true, WEIGHTED>(i, cuv, nullptr, nullptr, cw, cs);
-                    lowd_edge(L, r);
-                    cs[i] = r.s;
-                }
-                ring_issue<WEIGHTED>(c_issue, q_issue < Q, CO, tid, cuv, cw, cs, si[j], suv[j], ss[j], sw[j]);
+                if (vi[j] >= 0) __stcg(cs + vi[j], update4<WEIGHTED>(L, ruv[j], rs[j], rw[j]));
+                class_overflow<WEIGHTED>(L, c, CO, tid, B, cuv, cw, cs);
+                ring_issue<WEIGHTED>(c_issue, q_issue < Q, CO, tid, cuv, cw, cs, vi[j], ruv[j], rs[j], rw[j]);
                 c_issue = (c_issue + 1 == C) ? 0 : c_issue + 1;
                 ++q_issue;
                 c = (c + 1 == C) ? 0 : c + 1;
@@ -312,45 +311,63 @@ k_sweep_ring(int32_t n, int32_t C, const int32_t* __restrict__ coff, int32_t co_
     for (int i = tid; i < n; i += B) l[i] = L[i];
 }
 
+// Schedules with fewer classes than the ring depth: same layout, no prefetch ring.
 template <bool WEIGHTED>
-cudaError_t launch_ring(lowd_ctx* h, int32_t passes) {
-    const size_t lbytes = sizeof(float) * (size_t)h->n;
+__global__ void __launch_bounds__(kVecThreads, 1)
+k_sweep_simple(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint4* __restrict__ cuv,
+               const float4* __restrict__ cw, float4* __restrict__ cs, float* __restrict__ l,
+               int32_t passes) {
+    extern __shared__ float L[];
+    const int tid = threadIdx.x;
+    const int B = blockDim.x;
+    for (int i = tid; i <= n; i += B) L[i] = i < n ? l[i] : 0.0f;
+    __syncthreads();
+    for (int32_t t = 0; t < passes; ++t)
+        for (int32_t c = 0; c < C; ++c) {
+            const int32_t e4 = coff[c + 1] >> 2;
+            for (int32_t i = (coff[c] >> 2) + tid; i < e4; i += B) {
+                float4 w4 = WEIGHTED ? __ldg(cw + i) : float4{1.f, 1.f, 1.f, 1.f};
+                float4 r = update4<WEIGHTED>(L, __ldg(cuv + i), __ldcg(cs + i), w4);
+                __stcg(cs + i, r);
+            }
+            __syncthreads();
+        }
+    for (int i = tid; i < n; i += B) l[i] = L[i];
+}
+
+template <bool WEIGHTED>
+cudaError_t launch_sweep(lowd_ctx* h, int32_t passes) {
+    const size_t lbytes = sizeof(float) * ((size_t)h->n + 1);
     const size_t cbytes = sizeof(int32_t) * ((size_t)h->C + 1);
     const size_t budget = 227 * 1024;
     const int co_smem = lbytes + cbytes <= budget ? 1 : 0;
     const size_t smem = lbytes + (co_smem ? cbytes : 0);
-    int32_t maxc = 0;
-    for (int32_t c = 0; c < h->C; ++c) maxc = max(maxc, h->coff_h[c + 1] - h->coff_h[c]);
-    int threads = ((maxc + 31) / 32) * 32;
-    if (threads < 128) threads = 128;
-    if (threads > kCtaThreads) threads = kCtaThreads;
-    auto kern = k_sweep_ring<WEIGHTED>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    LOWD_LAUNCH(kern, 1, threads, smem, h->st, h->n, h->C, h->coff, co_smem, h->cuv, h->cw, h->cs, h->l,
-                passes);
-    return cudaGetLastError();
-}
-
-template <bool PACKED, bool WEIGHTED>
-cudaError_t launch_cta(lowd_ctx* h, int32_t passes) {
-    size_t smem = sizeof(float) * (size_t)(h->n > 0 ? h->n : 1);
-    auto kern = k_sweep_cta<PACKED, WEIGHTED>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    LOWD_LAUNCH(kern, 1, kCtaThreads, smem, h->st, h->n, h->C, h->coff, h->cuv, h->cu, h->cv, h->cw, h->cs, h->l, passes);
+    int32_t maxv = 0;  // largest class, in 4-edge vectors
+    for (int32_t c = 0; c < h->C; ++c) maxv = max(maxv, (h->coff_h[c + 1] - h->coff_h[c]) >> 2);
+    int threads = ((maxv + 31) / 32) * 32;
+    if (threads < 64) threads = 64;
+    if (threads > kVecThreads) threads = kVecThreads;
+    const uint4* cuv = reinterpret_cast<const uint4*>(h->cuv);
+    const float4* cw = reinterpret_cast<const float4*>(h->cw);
+    float4* cs = reinterpret_cast<float4*>(h->cs);
+    constexpr int kRing = WEIGHTED ? kRingW : kRingU;
+    if (h->C >= kRing) {
+        auto kern = k_sweep_vec<WEIGHTED, kRing>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        LOWD_LAUNCH(kern, 1, threads, smem, h->st, h->n, h->C, h->coff, co_smem, cuv, cw, cs, h->l, passes);
+    } else {
+        auto kern = k_sweep_simple<WEIGHTED>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lbytes);
+        if (e != cudaSuccess) return e;
+        LOWD_LAUNCH(kern, 1, threads, lbytes, h->st, h->n, h->C, h->coff, cuv, cw, cs, h->l, passes);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t run_passes(lowd_ctx* h, int32_t passes) {
     if (passes <= 0 || h->m == 0) return cudaSuccess;
-    const bool packed = h->cuv != nullptr;
-    const bool weighted = h->cw != nullptr;
-    if (packed && h->C >= kRing) return weighted ? launch_ring<true>(h, passes) : launch_ring<false>(h, passes);
-    if (packed && weighted) return launch_cta<true, true>(h, passes);
-    if (packed) return launch_cta<true, false>(h, passes);
-    if (weighted) return launch_cta<false, true>(h, passes);
-    return launch_cta<false, false>(h, passes);
+    return h->cw ? launch_sweep<true>(h, passes) : launch_sweep<false>(h, passes);
 }
 
 }  // namespace
@@ -361,7 +378,10 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
     cudaStream_t st = h->st;
     const int64_t m = h->m;
     const int32_t n = h->n;
-    if (schedule_req == 2) return LOWD_ERR_TOO_LARGE;  // grid schedule not available in this build
+    if (schedule_req == 2) {
+        snprintf(h->err, sizeof(h->err), "the grid schedule is not part of this build");
+        return LOWD_ERR_TOO_LARGE;
+    }
     if (n > LOWD_SMEM_NODES) {
         snprintf(h->err, sizeof(h->err), "current graph has %d nodes; the shared-memory sweep holds at most %d",
                  n, LOWD_SMEM_NODES);
@@ -369,9 +389,12 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
     }
     uint32_t* key[2] = {nullptr, nullptr};
     int32_t* val[2] = {nullptr, nullptr};
-    int32_t *head = nullptr, *hpos = nullptr;
+    int32_t *head = nullptr, *hpos = nullptr, *pcnt = nullptr;
     lowd_status s = LOWD_OK;
-    auto cleanup = [&]() { dfree(&key[0]); dfree(&key[1]); dfree(&val[0]); dfree(&val[1]); dfree(&head); dfree(&hpos); };
+    auto cleanup = [&]() {
+        dfree(&key[0]); dfree(&key[1]); dfree(&val[0]); dfree(&val[1]);
+        dfree(&head); dfree(&hpos); dfree(&pcnt);
+    };
     do {
         if ((s = h->need_tmp(lowd_sort_tmp_bytes(m > n ? m : n)))) break;
         if ((s = dalloc(h, &key[0], m))) break;
@@ -395,27 +418,36 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
             C = *(int32_t*)h->h_pin;
         }
         h->C = C;
+        // real and padded class offsets
+        if ((s = dalloc(h, &h->coff_real, (size_t)C + 1))) break;
         if ((s = dalloc(h, &h->coff, (size_t)C + 1))) break;
-        if (m > 0) LOWD_LAUNCH(k_class_offsets, grid_for(m), kT, 0, st, head, hpos, m, C, h->coff);
-        else cudaMemsetAsync(h->coff, 0, sizeof(int32_t), st);
+        if ((s = dalloc(h, &pcnt, (size_t)C + 1))) break;
+        if (m > 0) {
+            LOWD_LAUNCH(k_class_offsets, grid_for(m), kT, 0, st, head, hpos, m, C, h->coff_real);
+            LOWD_LAUNCH(k_pad_sizes, grid_for(C), kT, 0, st, h->coff_real, C, pcnt);
+            scan_exclusive<int32_t>(pcnt, h->coff, C, h->coff + C, h->tmp, st);
+        } else {
+            cudaMemsetAsync(h->coff_real, 0, sizeof(int32_t), st);
+            cudaMemsetAsync(h->coff, 0, sizeof(int32_t), st);
+        }
         h->coff_h = (int32_t*)malloc(sizeof(int32_t) * ((size_t)C + 1));
         if (!h->coff_h) { s = LOWD_ERR_OUT_OF_MEMORY; break; }
-        if (cudaMemcpyAsync(h->coff_h, h->coff, sizeof(int32_t) * ((size_t)C + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-            { s = h->fail(cudaGetLastError()); break; }
-        // the class-major permutation
-        h->perm = val[cur];
-        val[cur] = nullptr;
-        if (n <= 65536) { if ((s = dalloc(h, &h->cuv, m))) break; }
-        else {
-            if ((s = dalloc(h, &h->cu, m))) break;
-            if ((s = dalloc(h, &h->cv, m))) break;
-        }
-        if (h->w && (s = dalloc(h, &h->cw, m))) break;
-        if ((s = dalloc(h, &h->cs, m))) break;
-        if ((s = dalloc(h, &h->l, n))) break;
+        if (cudaMemcpyAsync(h->coff_h, h->coff, sizeof(int32_t) * ((size_t)C + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
+        const int64_t m_pad = h->coff_h[C];
+        h->m_pad = m_pad;
+        if ((s = dalloc(h, &h->perm, m_pad))) break;
+        if (m_pad > 0) LOWD_LAUNCH(k_fill_perm, grid_for(m_pad), kT, 0, st, h->perm, m_pad);
         if (m > 0)
-            LOWD_LAUNCH(k_gather_streams, grid_for(m), kT, 0, st, h->perm, m, h->u, h->v, h->w, init_splits_canon,
-                                                         h->cuv, h->cu, h->cv, h->cw, h->cs);
+            LOWD_LAUNCH(k_scatter_padded, grid_for(m), kT, 0, st, val[cur], head, hpos, h->coff_real, h->coff, m,
+                        h->perm);
+        if ((s = dalloc(h, &h->cuv, m_pad))) break;
+        if (h->w && (s = dalloc(h, &h->cw, m_pad))) break;
+        if ((s = dalloc(h, &h->cs, m_pad))) break;
+        if ((s = dalloc(h, &h->l, (size_t)n + 1))) break;
+        if (m_pad > 0)
+            LOWD_LAUNCH(k_gather_streams, grid_for(m_pad), kT, 0, st, h->perm, m_pad, n, h->u, h->v, h->w,
+                        init_splits_canon, h->cuv, h->cw, h->cs);
         if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
         h->sched = 1;
         h->inited = 1;
@@ -433,7 +465,7 @@ lowd_status lowd_sweep_rederive(lowd_ctx* h, double* stats3) {
     LOWD_TRY(dalloc(h, &L64, h->n));
     cudaMemsetAsync(L64, 0, sizeof(double) * (size_t)h->n, st);
     cudaMemsetAsync(h->d_stats, 0, 3 * sizeof(double), st);
-    if (h->m > 0) LOWD_LAUNCH(k_rederive, grid_for(h->m), kT, 0, st, h->m, h->cuv, h->cu, h->cv, h->cw, h->cs, L64);
+    if (h->m_pad > 0) LOWD_LAUNCH(k_rederive, grid_for(h->m_pad), kT, 0, st, h->m_pad, h->cuv, h->cw, h->cs, L64);
     LOWD_LAUNCH(k_load_stats, grid_for(h->n), kT, 0, st, L64, h->n, h->l, h->d_stats);
     double tmp3[3];
     cudaError_t e = cudaGetLastError();
@@ -446,15 +478,35 @@ lowd_status lowd_sweep_rederive(lowd_ctx* h, double* stats3) {
 }
 
 lowd_status lowd_sweep_splits_canonical(lowd_ctx* h, float* out_dev) {
-    if (h->m > 0) LOWD_LAUNCH(k_splits_to_canonical, grid_for(h->m), kT, 0, h->st, h->perm, h->m, h->cs, out_dev);
+    if (h->m_pad > 0)
+        LOWD_LAUNCH(k_splits_to_canonical, grid_for(h->m_pad), kT, 0, h->st, h->perm, h->m_pad, h->cs, out_dev);
     LOWD_CK_LAUNCH();
     return LOWD_OK;
 }
 
 lowd_status lowd_sweep_load_canonical(lowd_ctx* h, const float* splits_dev) {
-    if (h->m > 0) LOWD_LAUNCH(k_splits_from_canonical, grid_for(h->m), kT, 0, h->st, h->perm, h->m, splits_dev, h->cs);
+    if (h->m_pad > 0)
+        LOWD_LAUNCH(k_splits_from_canonical, grid_for(h->m_pad), kT, 0, h->st, h->perm, h->m_pad, splits_dev, h->cs);
     LOWD_CK_LAUNCH();
     return LOWD_OK;
+}
+
+// The update order as canonical edge ids (padding removed) into out_dev [m].
+lowd_status lowd_sweep_edge_order(lowd_ctx* h, int32_t* out_dev) {
+    int32_t *f = nullptr, *pos = nullptr;
+    LOWD_TRY(h->need_tmp(lowd_sort_tmp_bytes(h->m_pad)));
+    LOWD_TRY(dalloc(h, &f, h->m_pad));
+    lowd_status s = dalloc(h, &pos, h->m_pad);
+    if (s == LOWD_OK && h->m_pad > 0) {
+        LOWD_LAUNCH(k_real_flags, grid_for(h->m_pad), kT, 0, h->st, h->perm, h->m_pad, f);
+        scan_exclusive<int32_t>(f, pos, h->m_pad, nullptr, h->tmp, h->st);
+        LOWD_LAUNCH(k_compact_perm, grid_for(h->m_pad), kT, 0, h->st, h->perm, f, pos, h->m_pad, out_dev);
+        if (cudaGetLastError() != cudaSuccess) s = h->fail(cudaGetLastError());
+    }
+    cudaStreamSynchronize(h->st);
+    dfree(&f);
+    dfree(&pos);
+    return s;
 }
 
 lowd_status lowd_sweep_run(lowd_ctx* h, int32_t k, const lowd_options* opt, lowd_stats* out) {
