@@ -76,15 +76,19 @@ __global__ void k_fill_perm(int32_t* __restrict__ perm_pad, int64_t m_pad) {
         perm_pad[i] = -1;
 }
 
-// Real position i (class-major, unpadded) -> padded position.
+// Real position i (class-major, unpadded) -> padded, interleaved position.
 __global__ void k_scatter_padded(const int32_t* __restrict__ perm, const int32_t* __restrict__ head,
                                  const int32_t* __restrict__ hpos, const int32_t* __restrict__ coff_real,
                                  const int32_t* __restrict__ coff_pad, int64_t m,
                                  int32_t* __restrict__ perm_pad) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t c = hpos[i] + head[i] - 1;
-        perm_pad[coff_pad[c] + (i - coff_real[c])] = perm[i];
+        // rank r of the class goes to component r / V of vector r % V (V vectors in the
+        // padded class), so lane t of a warp holds ranks t, V + t, 2V + t, 3V + t
+        const int32_t c = hpos[i] + head[i] - 1;
+        const int32_t r = (int32_t)(i - coff_real[c]);
+        const int32_t V = (coff_pad[c + 1] - coff_pad[c]) >> 2;
+        perm_pad[coff_pad[c] + 4 * (r % V) + r / V] = perm[i];
     }
 }
 
@@ -239,7 +243,7 @@ constexpr int kRingW = 6;  // ring depth, weighted (one more vector per slot)
 constexpr int kVecThreads = 512;
 
 template <bool WEIGHTED>
-__device__ __forceinline__ void ring_issue(int32_t cls, bool ok, const int32_t* CO, int tid,
+__device__ __forceinline__ void ring_issue(int32_t cls, bool ok, const int32_t* __restrict__ CO, int tid,
                                            const uint4* __restrict__ cuv, const float4* __restrict__ cw,
                                            const float4* __restrict__ cs, int32_t& vi, uint4& ruv,
                                            float4& rs, float4& rw) {
@@ -256,7 +260,7 @@ __device__ __forceinline__ void ring_issue(int32_t cls, bool ok, const int32_t* 
 }
 
 template <bool WEIGHTED>
-__device__ __forceinline__ void class_overflow(float* L, int32_t cls, const int32_t* CO, int tid, int B,
+__device__ __forceinline__ void class_overflow(float* L, int32_t cls, const int32_t* __restrict__ CO, int tid, int B,
                                                const uint4* __restrict__ cuv, const float4* __restrict__ cw,
                                                float4* __restrict__ cs) {
     const int32_t e4 = CO[cls + 1] >> 2;
@@ -267,9 +271,9 @@ __device__ __forceinline__ void class_overflow(float* L, int32_t cls, const int3
     }
 }
 
-template <bool WEIGHTED, int kRing>
+template <bool WEIGHTED, int kRing, bool CO_SMEM>
 __global__ void __launch_bounds__(kVecThreads, 1)
-k_sweep_vec(int32_t n, int32_t C, const int32_t* __restrict__ coff, int32_t co_smem,
+k_sweep_vec(int32_t n, int32_t C, const int32_t* __restrict__ coff,
             const uint4* __restrict__ cuv, const float4* __restrict__ cw, float4* __restrict__ cs,
             float* __restrict__ l, int32_t passes) {
     extern __shared__ float L[];
@@ -277,10 +281,10 @@ k_sweep_vec(int32_t n, int32_t C, const int32_t* __restrict__ coff, int32_t co_s
     const int tid = threadIdx.x;
     const int B = blockDim.x;
     for (int i = tid; i <= n; i += B) L[i] = i < n ? l[i] : 0.0f;
-    if (co_smem)
+    if (CO_SMEM)
         for (int i = tid; i <= C; i += B) COs[i] = coff[i];
     __syncthreads();
-    const int32_t* CO = co_smem ? COs : coff;
+    const int32_t* __restrict__ CO = CO_SMEM ? COs : coff;
     const int64_t Q = (int64_t)C * passes;
     int32_t vi[kRing];
     uint4 ruv[kRing];
@@ -352,10 +356,10 @@ cudaError_t launch_sweep(lowd_ctx* h, int32_t passes) {
     float4* cs = reinterpret_cast<float4*>(h->cs);
     constexpr int kRing = WEIGHTED ? kRingW : kRingU;
     if (h->C >= kRing) {
-        auto kern = k_sweep_vec<WEIGHTED, kRing>;
+        auto kern = co_smem ? k_sweep_vec<WEIGHTED, kRing, true> : k_sweep_vec<WEIGHTED, kRing, false>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        LOWD_LAUNCH(kern, 1, threads, smem, h->st, h->n, h->C, h->coff, co_smem, cuv, cw, cs, h->l, passes);
+        LOWD_LAUNCH(kern, 1, threads, smem, h->st, h->n, h->C, h->coff, cuv, cw, cs, h->l, passes);
     } else {
         auto kern = k_sweep_simple<WEIGHTED>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lbytes);
