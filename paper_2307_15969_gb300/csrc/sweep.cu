@@ -315,6 +315,198 @@ k_sweep_vec(int32_t n, int32_t C, const int32_t* __restrict__ coff,
     for (int i = tid; i < n; i += B) l[i] = L[i];
 }
 
+// ------------------------------------------------------------------ bulk-copy staged sweep
+//
+// A CTA barrier waits for the issuing threads' outstanding global loads and stores, so a
+// sweep that prefetches into registers pays a memory round trip per class.  Here the
+// edge data never passes through registers on its way in or out: a producer warp moves
+// each class segment (packed ends, splits, weights) global -> shared with cp.async.bulk,
+// completion signalled on one mbarrier per stage, and writes the updated splits back
+// shared -> global with bulk stores.  Consumers (all other warps) wait on the stage's
+// mbarrier, update the loads in shared memory, write the new splits into the stage, and
+// meet at the class barrier.  Stage q mod S holds class q mod C of the class stream;
+// after class q the producer stores stage q, then refills stage q-1 with stream position
+// q+S-1 once that stage's previous store has been read out (bulk wait_group.read 1).  The
+// splits of a class are re-read one pass later; wait_group 8 keeps at most 8 stores in
+// flight, and C >= S + 7 makes the store of the previous pass older than those 8.
+// Every wait on an mbarrier is bounded; on expiry the kernel records an error flag and
+// all threads leave the loop together.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void bulk_wait() {
+    asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+constexpr int kTmaConsumers = 512;
+constexpr int kTmaMaxStages = 8;
+constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait rounds before giving up
+
+struct TmaLayout {
+    uint32_t bars, L, CO, stages, stage_bytes, arr_bytes, total;
+};
+
+__host__ __device__ inline TmaLayout tma_layout(int32_t n, int32_t C, int32_t S, int32_t Emax, bool weighted) {
+    TmaLayout t;
+    t.bars = 0;
+    t.L = 8u * kTmaMaxStages;
+    t.CO = t.L + 4u * (uint32_t)(n + 1);
+    uint32_t end = t.CO + 4u * (uint32_t)(C + 1);
+    t.stages = (end + 127u) & ~127u;
+    t.arr_bytes = ((4u * (uint32_t)Emax) + 127u) & ~127u;
+    t.stage_bytes = t.arr_bytes * (weighted ? 3u : 2u);
+    t.total = t.stages + t.stage_bytes * (uint32_t)S;
+    return t;
+}
+
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(kTmaConsumers + 32, 1)
+k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32_t* __restrict__ cuv,
+            const float* __restrict__ cw, float* __restrict__ cs, float* __restrict__ l, int32_t passes,
+            int32_t S, int32_t Emax, int32_t* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const TmaLayout lay = tma_layout(n, C, S, Emax, WEIGHTED);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + lay.bars);
+    float* L = reinterpret_cast<float*>(smem + lay.L);
+    int32_t* CO = reinterpret_cast<int32_t*>(smem + lay.CO);
+    __shared__ int32_t abort_flag;
+    const int tid = threadIdx.x;
+    const int nc = blockDim.x - 32;          // consumer threads; the last warp produces
+    const bool is_producer = tid >= nc;
+    const bool lead = tid == nc;             // lane 0 of the producer warp
+    auto stage_uv = [&](int32_t k) { return reinterpret_cast<uint32_t*>(smem + lay.stages + lay.stage_bytes * k); };
+    auto stage_s = [&](int32_t k) {
+        return reinterpret_cast<float*>(smem + lay.stages + lay.stage_bytes * k + lay.arr_bytes);
+    };
+    auto stage_w = [&](int32_t k) {
+        return reinterpret_cast<float*>(smem + lay.stages + lay.stage_bytes * k + 2 * lay.arr_bytes);
+    };
+    for (int i = tid; i <= n; i += blockDim.x) L[i] = i < n ? l[i] : 0.0f;
+    for (int i = tid; i <= C; i += blockDim.x) CO[i] = coff[i];
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    const int64_t Q = (int64_t)C * passes;
+    auto fill = [&](int64_t p) {   // producer lead only: stream position p -> stage p mod S
+        const int32_t k = (int32_t)(p % S);
+        const int32_t c = (int32_t)(p % C);
+        const int32_t beg = CO[c];
+        const uint32_t bytes = 4u * (uint32_t)(CO[c + 1] - beg);
+        mbar_expect_tx(&bars[k], bytes * (WEIGHTED ? 3u : 2u));
+        bulk_g2s(stage_uv(k), cuv + beg, bytes, &bars[k]);
+        bulk_g2s(stage_s(k), cs + beg, bytes, &bars[k]);
+        if (WEIGHTED) bulk_g2s(stage_w(k), cw + beg, bytes, &bars[k]);
+    };
+    if (lead)
+        for (int64_t p = 0; p < S - 1 && p < Q; ++p) fill(p);
+    int32_t c = 0;
+    int64_t q = 0;
+    for (; q < Q; ++q) {
+        const int32_t k = (int32_t)(q % S);
+        if (!is_producer) {
+            const uint32_t parity = (uint32_t)((q / S) & 1);
+            uint32_t spins = 0;
+            bool ok = mbar_try_wait(&bars[k], parity);
+            while (!ok && ++spins < kWaitLimit) ok = mbar_try_wait(&bars[k], parity);
+            if (!ok) {
+                abort_flag = 1;
+            } else {
+                const int32_t V = (CO[c + 1] - CO[c]) >> 2;
+                const uint4* suv = reinterpret_cast<const uint4*>(stage_uv(k));
+                float4* ss = reinterpret_cast<float4*>(stage_s(k));
+                const float4* sw = reinterpret_cast<const float4*>(stage_w(k));
+                for (int32_t v = tid; v < V; v += nc) {
+                    float4 w4 = WEIGHTED ? sw[v] : float4{1.f, 1.f, 1.f, 1.f};
+                    ss[v] = update4<WEIGHTED>(L, suv[v], ss[v], w4);
+                }
+                fence_proxy_async_smem();
+            }
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        if (lead) {
+            const int32_t beg = CO[c];
+            bulk_s2g(cs + beg, stage_s(k), 4u * (uint32_t)(CO[c + 1] - beg));
+            bulk_commit();
+            if (q + S - 1 < Q) {
+                bulk_wait<8>();
+                bulk_wait_read<1>();
+                fill(q + S - 1);
+            }
+        }
+        c = (c + 1 == C) ? 0 : c + 1;
+    }
+    if (lead) {
+        if (abort_flag) {
+            // give the loads already issued a bounded chance to land before leaving
+            for (int64_t p = q; p < q + S - 1 && p < Q; ++p) {
+                uint32_t spins = 0;
+                while (!mbar_try_wait(&bars[p % S], (uint32_t)((p / S) & 1)) && ++spins < kWaitLimit) {
+                }
+            }
+            atomicOr(err, 1);
+        }
+        bulk_wait<0>();
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) l[i] = L[i];
+}
+
 // Schedules with fewer classes than the ring depth: same layout, no prefetch ring.
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(kVecThreads, 1)
@@ -340,7 +532,37 @@ k_sweep_simple(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uin
 }
 
 template <bool WEIGHTED>
+cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* launched) {
+    *launched = false;
+    const size_t budget = 227 * 1024;
+    int32_t S = kTmaMaxStages;
+    TmaLayout lay = tma_layout(h->n, h->C, S, maxlen, WEIGHTED);
+    while (S > 3 && lay.total > budget) {
+        --S;
+        lay = tma_layout(h->n, h->C, S, maxlen, WEIGHTED);
+    }
+    if (lay.total > budget || h->C < S + 7) return cudaSuccess;
+    int threads = (((maxlen >> 2) + 31) / 32) * 32;
+    if (threads < 64) threads = 64;
+    if (threads > kTmaConsumers) threads = kTmaConsumers;
+    auto kern = k_sweep_tma<WEIGHTED>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
+    if (e != cudaSuccess) return e;
+    LOWD_LAUNCH(kern, 1, threads + 32, lay.total, h->st, h->n, h->C, h->coff, h->cuv, h->cw, h->cs, h->l, passes,
+                S, maxlen, h->d_i32 + 8);
+    *launched = true;
+    return cudaGetLastError();
+}
+
+template <bool WEIGHTED>
 cudaError_t launch_sweep(lowd_ctx* h, int32_t passes) {
+    {
+        int32_t maxlen = 0;
+        for (int32_t c = 0; c < h->C; ++c) maxlen = max(maxlen, h->coff_h[c + 1] - h->coff_h[c]);
+        bool launched = false;
+        cudaError_t e = launch_sweep_tma<WEIGHTED>(h, passes, maxlen, &launched);
+        if (e != cudaSuccess || launched) return e;
+    }
     const size_t lbytes = sizeof(float) * ((size_t)h->n + 1);
     const size_t cbytes = sizeof(int32_t) * ((size_t)h->C + 1);
     const size_t budget = 227 * 1024;
@@ -371,6 +593,8 @@ cudaError_t launch_sweep(lowd_ctx* h, int32_t passes) {
 
 cudaError_t run_passes(lowd_ctx* h, int32_t passes) {
     if (passes <= 0 || h->m == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(h->d_i32 + 8, 0, sizeof(int32_t), h->st);
+    if (e != cudaSuccess) return e;
     return h->cw ? launch_sweep<true>(h, passes) : launch_sweep<false>(h, passes);
 }
 
@@ -528,6 +752,12 @@ lowd_status lowd_sweep_run(lowd_ctx* h, int32_t k, const lowd_options* opt, lowd
         int32_t step = k - done;
         if (o.check_every > 0 && o.check_every < step) step = o.check_every;
         LOWD_CK(run_passes(h, step));
+        LOWD_CK(cudaMemcpyAsync(h->h_pin + 8, h->d_i32 + 8, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+        LOWD_CK(cudaStreamSynchronize(h->st));
+        if (*(int32_t*)(h->h_pin + 8) != 0) {
+            snprintf(h->err, sizeof(h->err), "sweep: a bounded wait on a staged copy expired");
+            return LOWD_ERR_CUDA;
+        }
         done += step;
         h->iters += step;
         if (o.check_every > 0) {
