@@ -400,7 +400,7 @@ struct TmaLayout {
 __host__ __device__ inline TmaLayout tma_layout(int32_t n, int32_t C, int32_t S, int32_t Emax, bool weighted) {
     TmaLayout t;
     t.bars = 0;
-    t.L = 8u * kTmaMaxStages;
+    t.L = 16u * kTmaMaxStages;   // S full + S empty mbarriers
     t.CO = t.L + 4u * (uint32_t)(n + 1);
     uint32_t end = t.CO + 4u * (uint32_t)(C + 1);
     t.stages = (end + 127u) & ~127u;
@@ -410,6 +410,14 @@ __host__ __device__ inline TmaLayout tma_layout(int32_t n, int32_t C, int32_t S,
     return t;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync(int nc) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nc) : "memory");
+}
+
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(kTmaConsumers + 32, 1)
 k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32_t* __restrict__ cuv,
@@ -417,14 +425,13 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
             int32_t S, int32_t Emax, int32_t* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     const TmaLayout lay = tma_layout(n, C, S, Emax, WEIGHTED);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + lay.bars);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bars);
+    uint64_t* empty = full + S;   // S full barriers, then S empty barriers
     float* L = reinterpret_cast<float*>(smem + lay.L);
     int32_t* CO = reinterpret_cast<int32_t*>(smem + lay.CO);
-    __shared__ int32_t abort_flag;
+    __shared__ volatile int32_t abort_flag;
     const int tid = threadIdx.x;
     const int nc = blockDim.x - 32;          // consumer threads; the last warp produces
-    const bool is_producer = tid >= nc;
-    const bool lead = tid == nc;             // lane 0 of the producer warp
     auto stage_uv = [&](int32_t k) { return reinterpret_cast<uint32_t*>(smem + lay.stages + lay.stage_bytes * k); };
     auto stage_s = [&](int32_t k) {
         return reinterpret_cast<float*>(smem + lay.stages + lay.stage_bytes * k + lay.arr_bytes);
@@ -436,75 +443,79 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
     for (int i = tid; i <= C; i += blockDim.x) CO[i] = coff[i];
     if (tid == 0) {
         abort_flag = 0;
-        for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], 1);
+        }
         fence_mbar_init();
         fence_proxy_async_smem();
     }
     __syncthreads();
     const int64_t Q = (int64_t)C * passes;
-    auto fill = [&](int64_t p) {   // producer lead only: stream position p -> stage p mod S
-        const int32_t k = (int32_t)(p % S);
-        const int32_t c = (int32_t)(p % C);
-        const int32_t beg = CO[c];
-        const uint32_t bytes = 4u * (uint32_t)(CO[c + 1] - beg);
-        mbar_expect_tx(&bars[k], bytes * (WEIGHTED ? 3u : 2u));
-        bulk_g2s(stage_uv(k), cuv + beg, bytes, &bars[k]);
-        bulk_g2s(stage_s(k), cs + beg, bytes, &bars[k]);
-        if (WEIGHTED) bulk_g2s(stage_w(k), cw + beg, bytes, &bars[k]);
-    };
-    if (lead)
-        for (int64_t p = 0; p < S - 1 && p < Q; ++p) fill(p);
-    int32_t c = 0;
-    int64_t q = 0;
-    for (; q < Q; ++q) {
-        const int32_t k = (int32_t)(q % S);
-        if (!is_producer) {
-            const uint32_t parity = (uint32_t)((q / S) & 1);
-            uint32_t spins = 0;
-            bool ok = mbar_try_wait(&bars[k], parity);
-            while (!ok && ++spins < kWaitLimit) ok = mbar_try_wait(&bars[k], parity);
-            if (!ok) {
-                abort_flag = 1;
-            } else {
-                const int32_t V = (CO[c + 1] - CO[c]) >> 2;
-                const uint4* suv = reinterpret_cast<const uint4*>(stage_uv(k));
-                float4* ss = reinterpret_cast<float4*>(stage_s(k));
-                const float4* sw = reinterpret_cast<const float4*>(stage_w(k));
-                for (int32_t v = tid; v < V; v += nc) {
-                    float4 w4 = WEIGHTED ? sw[v] : float4{1.f, 1.f, 1.f, 1.f};
-                    ss[v] = update4<WEIGHTED>(L, suv[v], ss[v], w4);
+    if (tid >= nc) {
+        // ---------------- producer warp (lane 0 works)
+        if (tid == nc) {
+            auto fill = [&](int64_t p) {
+                const int32_t k = (int32_t)(p % S);
+                const int32_t c = (int32_t)(p % C);
+                const int32_t beg = CO[c];
+                const uint32_t bytes = 4u * (uint32_t)(CO[c + 1] - beg);
+                mbar_expect_tx(&full[k], bytes * (WEIGHTED ? 3u : 2u));
+                bulk_g2s(stage_uv(k), cuv + beg, bytes, &full[k]);
+                bulk_g2s(stage_s(k), cs + beg, bytes, &full[k]);
+                if (WEIGHTED) bulk_g2s(stage_w(k), cw + beg, bytes, &full[k]);
+            };
+            for (int64_t p = 0; p < S - 1 && p < Q; ++p) fill(p);
+            int32_t c = 0;
+            for (int64_t q = 0; q < Q; ++q) {
+                const int32_t k = (int32_t)(q % S);
+                const uint32_t parity = (uint32_t)((q / S) & 1);
+                uint32_t spins = 0;
+                bool ok = mbar_try_wait(&empty[k], parity);
+                while (!ok && !abort_flag && ++spins < kWaitLimit) ok = mbar_try_wait(&empty[k], parity);
+                if (!ok) { abort_flag = 1; break; }
+                const int32_t beg = CO[c];
+                bulk_s2g(cs + beg, stage_s(k), 4u * (uint32_t)(CO[c + 1] - beg));
+                bulk_commit();
+                if (q + S - 1 < Q) {
+                    bulk_wait<8>();
+                    bulk_wait_read<1>();
+                    fill(q + S - 1);
                 }
-                fence_proxy_async_smem();
+                c = (c + 1 == C) ? 0 : c + 1;
             }
+            bulk_wait<0>();
+            if (abort_flag) atomicOr(err, 1);
         }
-        __syncthreads();
+        return;
+    }
+    // ---------------- consumers
+    int32_t c = 0;
+    for (int64_t q = 0; q < Q; ++q) {
+        const int32_t k = (int32_t)(q % S);
+        const uint32_t parity = (uint32_t)((q / S) & 1);
+        uint32_t spins = 0;
+        bool ok = mbar_try_wait(&full[k], parity);
+        while (!ok && !abort_flag && ++spins < kWaitLimit) ok = mbar_try_wait(&full[k], parity);
+        if (!ok) {
+            abort_flag = 1;
+        } else {
+            const int32_t V = (CO[c + 1] - CO[c]) >> 2;
+            const uint4* suv = reinterpret_cast<const uint4*>(stage_uv(k));
+            float4* ss = reinterpret_cast<float4*>(stage_s(k));
+            const float4* sw = reinterpret_cast<const float4*>(stage_w(k));
+            for (int32_t v = tid; v < V; v += nc) {
+                float4 w4 = WEIGHTED ? sw[v] : float4{1.f, 1.f, 1.f, 1.f};
+                ss[v] = update4<WEIGHTED>(L, suv[v], ss[v], w4);
+            }
+            fence_proxy_async_smem();
+        }
+        consumer_sync(nc);
         if (abort_flag) break;
-        if (lead) {
-            const int32_t beg = CO[c];
-            bulk_s2g(cs + beg, stage_s(k), 4u * (uint32_t)(CO[c + 1] - beg));
-            bulk_commit();
-            if (q + S - 1 < Q) {
-                bulk_wait<8>();
-                bulk_wait_read<1>();
-                fill(q + S - 1);
-            }
-        }
+        if (tid == 0) mbar_arrive(&empty[k]);
         c = (c + 1 == C) ? 0 : c + 1;
     }
-    if (lead) {
-        if (abort_flag) {
-            // give the loads already issued a bounded chance to land before leaving
-            for (int64_t p = q; p < q + S - 1 && p < Q; ++p) {
-                uint32_t spins = 0;
-                while (!mbar_try_wait(&bars[p % S], (uint32_t)((p / S) & 1)) && ++spins < kWaitLimit) {
-                }
-            }
-            atomicOr(err, 1);
-        }
-        bulk_wait<0>();
-    }
-    __syncthreads();
-    for (int i = tid; i < n; i += blockDim.x) l[i] = L[i];
+    for (int i = tid; i < n; i += nc) l[i] = L[i];
 }
 
 // Schedules with fewer classes than the ring depth: same layout, no prefetch ring.
