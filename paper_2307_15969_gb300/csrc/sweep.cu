@@ -324,11 +324,13 @@ k_sweep_vec(int32_t n, int32_t C, const int32_t* __restrict__ coff,
 // completion signalled on one mbarrier per stage, and writes the updated splits back
 // shared -> global with bulk stores.  Consumers (all other warps) wait on the stage's
 // mbarrier, update the loads in shared memory, write the new splits into the stage, and
-// meet at the class barrier.  Stage q mod S holds class q mod C of the class stream;
-// after class q the producer stores stage q, then refills stage q-1 with stream position
-// q+S-1 once that stage's previous store has been read out (bulk wait_group.read 1).  The
-// splits of a class are re-read one pass later; wait_group 8 keeps at most 8 stores in
-// flight, and C >= S + 7 makes the store of the previous pass older than those 8.
+// meet at a named barrier of the consumer warps only, then hand the stage back on its
+// "empty" mbarrier.  Stage q mod S holds class q mod C of the class stream.  The producer,
+// on its own timeline, waits for stage q to be handed back, stores its splits, and loads
+// stream position q + S - kStoreSlack into the stage whose store was issued kStoreSlack
+// steps earlier (bulk wait_group.read kStoreSlack).  The splits of a class are re-read one
+// pass later; wait_group kStoreGroups bounds the stores in flight, and
+// C >= S - kStoreSlack + kStoreGroups + 1 makes the previous pass's store older than them.
 // Every wait on an mbarrier is bounded; on expiry the kernel records an error flag and
 // all threads leave the loop together.
 
@@ -391,6 +393,8 @@ __device__ __forceinline__ void fence_mbar_init() {
 
 constexpr int kTmaConsumers = 512;
 constexpr int kTmaMaxStages = 8;
+constexpr int kStoreSlack = 3;    // bulk stores allowed to be still reading their stage
+constexpr int kStoreGroups = 16;  // bulk stores allowed in flight at all
 constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait rounds before giving up
 
 struct TmaLayout {
@@ -429,16 +433,10 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
     uint64_t* empty = full + S;   // S full barriers, then S empty barriers
     float* L = reinterpret_cast<float*>(smem + lay.L);
     int32_t* CO = reinterpret_cast<int32_t*>(smem + lay.CO);
+    unsigned char* stages = smem + lay.stages;
     __shared__ volatile int32_t abort_flag;
     const int tid = threadIdx.x;
     const int nc = blockDim.x - 32;          // consumer threads; the last warp produces
-    auto stage_uv = [&](int32_t k) { return reinterpret_cast<uint32_t*>(smem + lay.stages + lay.stage_bytes * k); };
-    auto stage_s = [&](int32_t k) {
-        return reinterpret_cast<float*>(smem + lay.stages + lay.stage_bytes * k + lay.arr_bytes);
-    };
-    auto stage_w = [&](int32_t k) {
-        return reinterpret_cast<float*>(smem + lay.stages + lay.stage_bytes * k + 2 * lay.arr_bytes);
-    };
     for (int i = tid; i <= n; i += blockDim.x) L[i] = i < n ? l[i] : 0.0f;
     for (int i = tid; i <= C; i += blockDim.x) CO[i] = coff[i];
     if (tid == 0) {
@@ -452,36 +450,44 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
     }
     __syncthreads();
     const int64_t Q = (int64_t)C * passes;
+    const int32_t ahead = S - kStoreSlack;   // classes loaded ahead of the consumers
     if (tid >= nc) {
         // ---------------- producer warp (lane 0 works)
         if (tid == nc) {
-            auto fill = [&](int64_t p) {
-                const int32_t k = (int32_t)(p % S);
-                const int32_t c = (int32_t)(p % C);
-                const int32_t beg = CO[c];
-                const uint32_t bytes = 4u * (uint32_t)(CO[c + 1] - beg);
-                mbar_expect_tx(&full[k], bytes * (WEIGHTED ? 3u : 2u));
-                bulk_g2s(stage_uv(k), cuv + beg, bytes, &full[k]);
-                bulk_g2s(stage_s(k), cs + beg, bytes, &full[k]);
-                if (WEIGHTED) bulk_g2s(stage_w(k), cw + beg, bytes, &full[k]);
+            // next fill: stream position pf, its stage kf and class cf
+            int64_t pf = 0;
+            int32_t kf = 0, cf = 0;
+            auto fill = [&]() {
+                const int32_t beg = CO[cf];
+                const uint32_t bytes = 4u * (uint32_t)(CO[cf + 1] - beg);
+                unsigned char* st = stages + (size_t)lay.stage_bytes * kf;
+                mbar_expect_tx(&full[kf], bytes * (WEIGHTED ? 3u : 2u));
+                bulk_g2s(st, cuv + beg, bytes, &full[kf]);
+                bulk_g2s(st + lay.arr_bytes, cs + beg, bytes, &full[kf]);
+                if (WEIGHTED) bulk_g2s(st + 2 * lay.arr_bytes, cw + beg, bytes, &full[kf]);
+                ++pf;
+                kf = (kf + 1 == S) ? 0 : kf + 1;
+                cf = (cf + 1 == C) ? 0 : cf + 1;
             };
-            for (int64_t p = 0; p < S - 1 && p < Q; ++p) fill(p);
-            int32_t c = 0;
+            while (pf < ahead && pf < Q) fill();
+            int32_t k = 0, c = 0;
+            uint32_t parity = 0;
             for (int64_t q = 0; q < Q; ++q) {
-                const int32_t k = (int32_t)(q % S);
-                const uint32_t parity = (uint32_t)((q / S) & 1);
                 uint32_t spins = 0;
                 bool ok = mbar_try_wait(&empty[k], parity);
                 while (!ok && !abort_flag && ++spins < kWaitLimit) ok = mbar_try_wait(&empty[k], parity);
                 if (!ok) { abort_flag = 1; break; }
                 const int32_t beg = CO[c];
-                bulk_s2g(cs + beg, stage_s(k), 4u * (uint32_t)(CO[c + 1] - beg));
+                bulk_s2g(cs + beg, stages + (size_t)lay.stage_bytes * k + lay.arr_bytes,
+                         4u * (uint32_t)(CO[c + 1] - beg));
                 bulk_commit();
-                if (q + S - 1 < Q) {
-                    bulk_wait<8>();
-                    bulk_wait_read<1>();
-                    fill(q + S - 1);
+                if (pf < Q) {
+                    // the stage to refill held position pf - S, stored kStoreSlack steps ago
+                    bulk_wait<kStoreGroups>();
+                    bulk_wait_read<kStoreSlack>();
+                    fill();
                 }
+                if (++k == S) { k = 0; parity ^= 1u; }
                 c = (c + 1 == C) ? 0 : c + 1;
             }
             bulk_wait<0>();
@@ -490,10 +496,9 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         return;
     }
     // ---------------- consumers
-    int32_t c = 0;
+    int32_t k = 0, c = 0;
+    uint32_t parity = 0;
     for (int64_t q = 0; q < Q; ++q) {
-        const int32_t k = (int32_t)(q % S);
-        const uint32_t parity = (uint32_t)((q / S) & 1);
         uint32_t spins = 0;
         bool ok = mbar_try_wait(&full[k], parity);
         while (!ok && !abort_flag && ++spins < kWaitLimit) ok = mbar_try_wait(&full[k], parity);
@@ -501,9 +506,10 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
             abort_flag = 1;
         } else {
             const int32_t V = (CO[c + 1] - CO[c]) >> 2;
-            const uint4* suv = reinterpret_cast<const uint4*>(stage_uv(k));
-            float4* ss = reinterpret_cast<float4*>(stage_s(k));
-            const float4* sw = reinterpret_cast<const float4*>(stage_w(k));
+            unsigned char* st = stages + (size_t)lay.stage_bytes * k;
+            const uint4* suv = reinterpret_cast<const uint4*>(st);
+            float4* ss = reinterpret_cast<float4*>(st + lay.arr_bytes);
+            const float4* sw = reinterpret_cast<const float4*>(st + 2 * lay.arr_bytes);
             for (int32_t v = tid; v < V; v += nc) {
                 float4 w4 = WEIGHTED ? sw[v] : float4{1.f, 1.f, 1.f, 1.f};
                 ss[v] = update4<WEIGHTED>(L, suv[v], ss[v], w4);
@@ -513,6 +519,7 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         consumer_sync(nc);
         if (abort_flag) break;
         if (tid == 0) mbar_arrive(&empty[k]);
+        if (++k == S) { k = 0; parity ^= 1u; }
         c = (c + 1 == C) ? 0 : c + 1;
     }
     for (int i = tid; i < n; i += nc) l[i] = L[i];
@@ -552,7 +559,9 @@ cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* 
         --S;
         lay = tma_layout(h->n, h->C, S, maxlen, WEIGHTED);
     }
-    if (lay.total > budget || h->C < S + 7) return cudaSuccess;
+    // a class's splits are re-read one pass later: its store must be older than the
+    // kStoreGroups stores allowed in flight when the producer loads it again
+    if (lay.total > budget || S - kStoreSlack < 2 || h->C < S - kStoreSlack + kStoreGroups + 1) return cudaSuccess;
     int threads = (((maxlen >> 2) + 31) / 32) * 32;
     if (threads < 64) threads = 64;
     if (threads > kTmaConsumers) threads = kTmaConsumers;
