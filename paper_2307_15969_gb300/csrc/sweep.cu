@@ -392,8 +392,8 @@ __device__ __forceinline__ void fence_mbar_init() {
 }
 
 constexpr int kTmaConsumers = 512;
-constexpr int kTmaMaxStages = 8;
-constexpr int kStoreSlack = 3;    // bulk stores allowed to be still reading their stage
+constexpr int kTmaMaxStages = 32;
+constexpr int kStoreSlack = 4;    // bulk stores allowed to be still reading their stage
 constexpr int kStoreGroups = 16;  // bulk stores allowed in flight at all
 constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait rounds before giving up
 
