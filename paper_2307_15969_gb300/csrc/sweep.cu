@@ -76,19 +76,15 @@ __global__ void k_fill_perm(int32_t* __restrict__ perm_pad, int64_t m_pad) {
         perm_pad[i] = -1;
 }
 
-// Real position i (class-major, unpadded) -> padded, interleaved position.
+// Real position i (class-major, unpadded) -> padded position.
 __global__ void k_scatter_padded(const int32_t* __restrict__ perm, const int32_t* __restrict__ head,
                                  const int32_t* __restrict__ hpos, const int32_t* __restrict__ coff_real,
                                  const int32_t* __restrict__ coff_pad, int64_t m,
                                  int32_t* __restrict__ perm_pad) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
-        // rank r of the class goes to component r / V of vector r % V (V vectors in the
-        // padded class), so lane t of a warp holds ranks t, V + t, 2V + t, 3V + t
         const int32_t c = hpos[i] + head[i] - 1;
-        const int32_t r = (int32_t)(i - coff_real[c]);
-        const int32_t V = (coff_pad[c + 1] - coff_pad[c]) >> 2;
-        perm_pad[coff_pad[c] + 4 * (r % V) + r / V] = perm[i];
+        perm_pad[coff_pad[c] + (i - coff_real[c])] = perm[i];
     }
 }
 
@@ -391,7 +387,7 @@ __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-constexpr int kTmaConsumers = 512;
+constexpr int kTmaConsumers = 992;   // one edge per consumer thread per class
 constexpr int kTmaMaxStages = 32;
 constexpr int kStoreSlack = 4;    // bulk stores allowed to be still reading their stage
 constexpr int kStoreGroups = 16;  // bulk stores allowed in flight at all
@@ -505,14 +501,17 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         if (!ok) {
             abort_flag = 1;
         } else {
-            const int32_t V = (CO[c + 1] - CO[c]) >> 2;
+            const int32_t len = CO[c + 1] - CO[c];
             unsigned char* st = stages + (size_t)lay.stage_bytes * k;
-            const uint4* suv = reinterpret_cast<const uint4*>(st);
-            float4* ss = reinterpret_cast<float4*>(st + lay.arr_bytes);
-            const float4* sw = reinterpret_cast<const float4*>(st + 2 * lay.arr_bytes);
-            for (int32_t v = tid; v < V; v += nc) {
-                float4 w4 = WEIGHTED ? sw[v] : float4{1.f, 1.f, 1.f, 1.f};
-                ss[v] = update4<WEIGHTED>(L, suv[v], ss[v], w4);
+            const uint32_t* suv = reinterpret_cast<const uint32_t*>(st);
+            float* ss = reinterpret_cast<float*>(st + lay.arr_bytes);
+            const float* sw = reinterpret_cast<const float*>(st + 2 * lay.arr_bytes);
+            for (int32_t r = tid; r < len; r += nc) {
+                const uint32_t uv = suv[r];
+                EdgeVal e{L[end_a(uv)], L[end_b(uv)], ss[r], WEIGHTED ? sw[r] : 1.0f};
+                ss[r] = lowd_transfer(e);
+                L[end_a(uv)] = e.la;
+                L[end_b(uv)] = e.lb;
             }
             fence_proxy_async_smem();
         }
@@ -562,7 +561,7 @@ cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* 
     // a class's splits are re-read one pass later: its store must be older than the
     // kStoreGroups stores allowed in flight when the producer loads it again
     if (lay.total > budget || S - kStoreSlack < 2 || h->C < S - kStoreSlack + kStoreGroups + 1) return cudaSuccess;
-    int threads = (((maxlen >> 2) + 31) / 32) * 32;
+    int threads = ((maxlen + 31) / 32) * 32;
     if (threads < 64) threads = 64;
     if (threads > kTmaConsumers) threads = kTmaConsumers;
     auto kern = k_sweep_tma<WEIGHTED>;
