@@ -492,34 +492,38 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         return;
     }
     // ---------------- consumers
+    // Warp 0 waits for the next stage before the class barrier; the barrier then orders
+    // that stage's data before every consumer's reads.
     int32_t k = 0, c = 0;
     uint32_t parity = 0;
-    for (int64_t q = 0; q < Q; ++q) {
+    auto wait_full = [&](int32_t kk, uint32_t par) {
         uint32_t spins = 0;
-        bool ok = mbar_try_wait(&full[k], parity);
-        while (!ok && !abort_flag && ++spins < kWaitLimit) ok = mbar_try_wait(&full[k], parity);
-        if (!ok) {
-            abort_flag = 1;
-        } else {
-            const int32_t len = CO[c + 1] - CO[c];
-            unsigned char* st = stages + (size_t)lay.stage_bytes * k;
-            const uint32_t* suv = reinterpret_cast<const uint32_t*>(st);
-            float* ss = reinterpret_cast<float*>(st + lay.arr_bytes);
-            const float* sw = reinterpret_cast<const float*>(st + 2 * lay.arr_bytes);
-            for (int32_t r = tid; r < len; r += nc) {
-                const uint32_t uv = suv[r];
-                EdgeVal e{L[end_a(uv)], L[end_b(uv)], ss[r], WEIGHTED ? sw[r] : 1.0f};
-                ss[r] = lowd_transfer(e);
-                L[end_a(uv)] = e.la;
-                L[end_b(uv)] = e.lb;
-            }
-            fence_proxy_async_smem();
+        bool ok = mbar_try_wait(&full[kk], par);
+        while (!ok && !abort_flag && ++spins < kWaitLimit) ok = mbar_try_wait(&full[kk], par);
+        if (!ok) abort_flag = 1;
+    };
+    if (tid < 32 && Q > 0) wait_full(0, 0);
+    consumer_sync(nc);
+    for (int64_t q = 0; q < Q && !abort_flag; ++q) {
+        const int32_t len = CO[c + 1] - CO[c];
+        unsigned char* st = stages + (size_t)lay.stage_bytes * k;
+        const uint32_t* suv = reinterpret_cast<const uint32_t*>(st);
+        float* ss = reinterpret_cast<float*>(st + lay.arr_bytes);
+        const float* sw = reinterpret_cast<const float*>(st + 2 * lay.arr_bytes);
+        for (int32_t r = tid; r < len; r += nc) {
+            const uint32_t uv = suv[r];
+            EdgeVal e{L[end_a(uv)], L[end_b(uv)], ss[r], WEIGHTED ? sw[r] : 1.0f};
+            ss[r] = lowd_transfer(e);
+            L[end_a(uv)] = e.la;
+            L[end_b(uv)] = e.lb;
         }
-        consumer_sync(nc);
-        if (abort_flag) break;
-        if (tid == 0) mbar_arrive(&empty[k]);
+        fence_proxy_async_smem();
+        const int32_t kprev = k;
         if (++k == S) { k = 0; parity ^= 1u; }
         c = (c + 1 == C) ? 0 : c + 1;
+        if (tid < 32 && q + 1 < Q) wait_full(k, parity);
+        consumer_sync(nc);
+        if (tid == 0) mbar_arrive(&empty[kprev]);
     }
     for (int i = tid; i < n; i += nc) l[i] = L[i];
 }
