@@ -51,7 +51,7 @@ def _sweep_hash():
 def _traffic_per_pass():
     """DRAM bytes per LOWD pass from the committed ncu summary, if it was taken on the
     current sweep kernel source."""
-    p = os.path.join(ROOT, "profiles", "sweep_rmat22_dram.json")
+    p = os.path.join(ROOT, "profiles", "k_sweep_tma_rmat22_dram.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -322,7 +322,7 @@ def main():
                    "l2": "flushed between timed steps (256 MB write); G's edge arrays (537 MB) exceed L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": (tpp * T if tpp is not None else None),
-                     "kernel": "k_sweep_cta", "peak_kind": peak_kind,
+                     "kernel": "k_sweep_tma", "peak_kind": peak_kind,
                      "launch_ms": sweep_s * 1e3, "bytes_per_update": BYTES_PER_UPDATE},
         "e2e": {"value": m_H * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},

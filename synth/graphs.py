@@ -339,6 +339,11 @@ WORKLOADS = {
                     block_size=128, block_p=0.5, weighted=True, block_weight_scale=3.0),
     "rmat18": dict(kind="rmat", scale=18, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=14,
                    block_size=256, block_p=0.5, weighted=False),
+    # Dense G(n, p) cores with the size and density of the pruned R-MAT cores (scale 22:
+    # 9,109 nodes at density 0.156; scale 18: 4,048 nodes at 0.125): small cases of the
+    # same sweep for profiling.
+    "dense9110": dict(kind="gnp", n=9110, p=0.156, seed=22),
+    "dense4096": dict(kind="gnp", n=4096, p=0.12, seed=1),
 }
 
 
@@ -349,4 +354,6 @@ def workload(name: str) -> Graph:
         return chung_lu(name=name, **spec)
     if kind == "rmat":
         return rmat(name=name, **spec)
+    if kind == "gnp":
+        return erdos_renyi(name=name, **spec)
     raise ValueError(kind)
