@@ -418,7 +418,21 @@ __device__ __forceinline__ void consumer_sync(int nc) {
     asm volatile("bar.sync 1, %0;" ::"r"(nc) : "memory");
 }
 
-template <bool WEIGHTED>
+// bar.sync over the consumer warps that also ORs a predicate across them
+__device__ __forceinline__ bool consumer_sync_or(int nc, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(nc)
+        : "memory");
+    return r != 0;
+}
+
+template <bool WEIGHTED, int E>
 __global__ void __launch_bounds__(kTmaConsumers + 32, 1)
 k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32_t* __restrict__ cuv,
             const float* __restrict__ cw, float* __restrict__ cs, float* __restrict__ l, int32_t passes,
@@ -445,18 +459,16 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         fence_proxy_async_smem();
     }
     __syncthreads();
-    const int64_t Q = (int64_t)C * passes;
+    const int32_t Q = C * passes;            // the launcher keeps C * passes < 2^31
     const int32_t ahead = S - kStoreSlack;   // classes loaded ahead of the consumers
     if (tid >= nc) {
         // ---------------- producer warp (lane 0 works)
         if (tid == nc) {
-            // next fill: stream position pf, its stage kf and class cf
-            int64_t pf = 0;
-            int32_t kf = 0, cf = 0;
+            int32_t pf = 0, kf = 0, cf = 0;  // next fill: stream position, stage, class
             auto fill = [&]() {
                 const int32_t beg = CO[cf];
                 const uint32_t bytes = 4u * (uint32_t)(CO[cf + 1] - beg);
-                unsigned char* st = stages + (size_t)lay.stage_bytes * kf;
+                unsigned char* st = stages + lay.stage_bytes * (uint32_t)kf;
                 mbar_expect_tx(&full[kf], bytes * (WEIGHTED ? 3u : 2u));
                 bulk_g2s(st, cuv + beg, bytes, &full[kf]);
                 bulk_g2s(st + lay.arr_bytes, cs + beg, bytes, &full[kf]);
@@ -468,13 +480,13 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
             while (pf < ahead && pf < Q) fill();
             int32_t k = 0, c = 0;
             uint32_t parity = 0;
-            for (int64_t q = 0; q < Q; ++q) {
+            for (int32_t q = 0; q < Q; ++q) {
                 uint32_t spins = 0;
                 bool ok = mbar_try_wait(&empty[k], parity);
                 while (!ok && !abort_flag && ++spins < kWaitLimit) ok = mbar_try_wait(&empty[k], parity);
                 if (!ok) { abort_flag = 1; break; }
                 const int32_t beg = CO[c];
-                bulk_s2g(cs + beg, stages + (size_t)lay.stage_bytes * k + lay.arr_bytes,
+                bulk_s2g(cs + beg, stages + lay.stage_bytes * (uint32_t)k + lay.arr_bytes,
                          4u * (uint32_t)(CO[c + 1] - beg));
                 bulk_commit();
                 if (pf < Q) {
@@ -492,38 +504,70 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         return;
     }
     // ---------------- consumers
-    // Warp 0 waits for the next stage before the class barrier; the barrier then orders
-    // that stage's data before every consumer's reads.
-    int32_t k = 0, c = 0;
-    uint32_t parity = 0;
-    auto wait_full = [&](int32_t kk, uint32_t par) {
+    // Thread t updates ranks t, t + nc, ..., t + (E-1) nc of each class: all their loads
+    // are issued before any store (the ends inside a class are distinct).  Warp 0 waits
+    // for the next stage before the class barrier; the barrier (which also ORs the abort
+    // flag) orders that stage's data before every consumer's reads.
+    auto wait_full = [&](int32_t kk, uint32_t par) -> bool {
         uint32_t spins = 0;
         bool ok = mbar_try_wait(&full[kk], par);
-        while (!ok && !abort_flag && ++spins < kWaitLimit) ok = mbar_try_wait(&full[kk], par);
-        if (!ok) abort_flag = 1;
+        while (!ok && ++spins < kWaitLimit) ok = mbar_try_wait(&full[kk], par);
+        return ok;
     };
-    if (tid < 32 && Q > 0) wait_full(0, 0);
-    consumer_sync(nc);
-    for (int64_t q = 0; q < Q && !abort_flag; ++q) {
-        const int32_t len = CO[c + 1] - CO[c];
-        unsigned char* st = stages + (size_t)lay.stage_bytes * k;
+    bool bad = false;
+    if (tid < 32 && Q > 0) bad = !wait_full(0, 0);
+    bad = consumer_sync_or(nc, bad);
+    int32_t k = 0, c = 0;
+    uint32_t parity = 0;
+    int32_t beg = CO[0];
+    for (int32_t q = 0; q < Q && !bad; ++q) {
+        const int32_t end = CO[c + 1];
+        const int32_t len = end - beg;
+        unsigned char* st = stages + lay.stage_bytes * (uint32_t)k;
         const uint32_t* suv = reinterpret_cast<const uint32_t*>(st);
         float* ss = reinterpret_cast<float*>(st + lay.arr_bytes);
         const float* sw = reinterpret_cast<const float*>(st + 2 * lay.arr_bytes);
-        for (int32_t r = tid; r < len; r += nc) {
-            const uint32_t uv = suv[r];
-            EdgeVal e{L[end_a(uv)], L[end_b(uv)], ss[r], WEIGHTED ? sw[r] : 1.0f};
-            ss[r] = lowd_transfer(e);
-            L[end_a(uv)] = e.la;
-            L[end_b(uv)] = e.lb;
+        for (int32_t r0 = tid; r0 < len; r0 += E * nc) {
+            uint32_t uv[E];
+            EdgeVal e[E];
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const int32_t r = r0 + j * nc;
+                uv[j] = r < len ? suv[r] : ((uint32_t)n | ((uint32_t)n << 16));
+                e[j].s = r < len ? ss[r] : 0.0f;
+                e[j].w = WEIGHTED ? (r < len ? sw[r] : 0.0f) : 1.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                e[j].la = L[end_a(uv[j])];
+                e[j].lb = L[end_b(uv[j])];
+            }
+            float ns[E];
+#pragma unroll
+            for (int j = 0; j < E; ++j) ns[j] = lowd_transfer(e[j]);
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const int32_t r = r0 + j * nc;
+                if (r < len) {
+                    L[end_a(uv[j])] = e[j].la;
+                    L[end_b(uv[j])] = e[j].lb;
+                    ss[r] = ns[j];
+                }
+            }
         }
         fence_proxy_async_smem();
         const int32_t kprev = k;
         if (++k == S) { k = 0; parity ^= 1u; }
         c = (c + 1 == C) ? 0 : c + 1;
-        if (tid < 32 && q + 1 < Q) wait_full(k, parity);
-        consumer_sync(nc);
+        beg = end == CO[C] ? 0 : end;
+        bool fail = false;
+        if (tid < 32 && q + 1 < Q) fail = !wait_full(k, parity);
+        bad = consumer_sync_or(nc, fail);
         if (tid == 0) mbar_arrive(&empty[kprev]);
+    }
+    if (bad && tid == 0) {
+        abort_flag = 1;
+        atomicOr(err, 1);
     }
     for (int i = tid; i < n; i += nc) l[i] = L[i];
 }
@@ -565,10 +609,13 @@ cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* 
     // a class's splits are re-read one pass later: its store must be older than the
     // kStoreGroups stores allowed in flight when the producer loads it again
     if (lay.total > budget || S - kStoreSlack < 2 || h->C < S - kStoreSlack + kStoreGroups + 1) return cudaSuccess;
-    int threads = ((maxlen + 31) / 32) * 32;
+    // edges per consumer thread: enough warps to hide latency, few enough to keep the
+    // per-class bookkeeping small
+    const int E = maxlen > 2048 ? 4 : (maxlen > 512 ? 2 : 1);
+    int threads = ((((maxlen + E - 1) / E) + 31) / 32) * 32;
     if (threads < 64) threads = 64;
     if (threads > kTmaConsumers) threads = kTmaConsumers;
-    auto kern = k_sweep_tma<WEIGHTED>;
+    auto kern = E == 4 ? k_sweep_tma<WEIGHTED, 4> : (E == 2 ? k_sweep_tma<WEIGHTED, 2> : k_sweep_tma<WEIGHTED, 1>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
     if (e != cudaSuccess) return e;
     LOWD_LAUNCH(kern, 1, threads + 32, lay.total, h->st, h->n, h->C, h->coff, h->cuv, h->cw, h->cs, h->l, passes,
@@ -618,7 +665,14 @@ cudaError_t run_passes(lowd_ctx* h, int32_t passes) {
     if (passes <= 0 || h->m == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(h->d_i32 + 8, 0, sizeof(int32_t), h->st);
     if (e != cudaSuccess) return e;
-    return h->cw ? launch_sweep<true>(h, passes) : launch_sweep<false>(h, passes);
+    // one launch covers at most 2^31 - 1 class updates
+    const int32_t per = (int32_t)(0x7fffffff / (h->C > 0 ? h->C : 1));
+    for (int32_t done = 0; done < passes && e == cudaSuccess;) {
+        const int32_t k = passes - done < per ? passes - done : per;
+        e = h->cw ? launch_sweep<true>(h, k) : launch_sweep<false>(h, k);
+        done += k;
+    }
+    return e;
 }
 
 }  // namespace
