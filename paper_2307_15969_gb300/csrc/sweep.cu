@@ -388,9 +388,9 @@ __device__ __forceinline__ void fence_mbar_init() {
 }
 
 constexpr int kTmaConsumers = 992;   // one edge per consumer thread per class
-constexpr int kTmaMaxStages = 32;
-constexpr int kStoreSlack = 4;    // bulk stores allowed to be still reading their stage
-constexpr int kStoreGroups = 16;  // bulk stores allowed in flight at all
+constexpr int kTmaMaxStages = 16;
+constexpr int kStoreSlack = 2;    // bulk stores allowed to be still reading their stage
+constexpr int kStoreGroups = 8;   // bulk stores allowed in flight at all
 constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait rounds before giving up
 
 struct TmaLayout {
@@ -414,7 +414,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void consumer_sync(int nc) {
+__device__ __forceinline__ void consumer_sync(int nc) {  // bar.sync over the consumer warps
     asm volatile("bar.sync 1, %0;" ::"r"(nc) : "memory");
 }
 
@@ -436,7 +436,7 @@ template <bool WEIGHTED, int E>
 __global__ void __launch_bounds__(kTmaConsumers + 32, 1)
 k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32_t* __restrict__ cuv,
             const float* __restrict__ cw, float* __restrict__ cs, float* __restrict__ l, int32_t passes,
-            int32_t S, int32_t Emax, int32_t* __restrict__ err) {
+            int32_t S, int32_t G, int32_t Emax, int32_t* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     const TmaLayout lay = tma_layout(n, C, S, Emax, WEIGHTED);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bars);
@@ -459,15 +459,17 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         fence_proxy_async_smem();
     }
     __syncthreads();
-    const int32_t Q = C * passes;            // the launcher keeps C * passes < 2^31
-    const int32_t ahead = S - kStoreSlack;   // classes loaded ahead of the consumers
+    const int32_t NC = (C + G - 1) / G;      // chunks of G classes per pass
+    const int32_t P = NC * passes;           // the launcher keeps this < 2^31
+    const int32_t ahead = S - kStoreSlack;   // chunks loaded ahead of the consumers
     if (tid >= nc) {
         // ---------------- producer warp (lane 0 works)
         if (tid == nc) {
-            int32_t pf = 0, kf = 0, cf = 0;  // next fill: stream position, stage, class
+            int32_t pf = 0, kf = 0, jf = 0;  // next fill: stream position, stage, chunk
             auto fill = [&]() {
-                const int32_t beg = CO[cf];
-                const uint32_t bytes = 4u * (uint32_t)(CO[cf + 1] - beg);
+                const int32_t beg = CO[jf * G];
+                const int32_t end = CO[min(jf * G + G, C)];
+                const uint32_t bytes = 4u * (uint32_t)(end - beg);
                 unsigned char* st = stages + lay.stage_bytes * (uint32_t)kf;
                 mbar_expect_tx(&full[kf], bytes * (WEIGHTED ? 3u : 2u));
                 bulk_g2s(st, cuv + beg, bytes, &full[kf]);
@@ -475,28 +477,28 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
                 if (WEIGHTED) bulk_g2s(st + 2 * lay.arr_bytes, cw + beg, bytes, &full[kf]);
                 ++pf;
                 kf = (kf + 1 == S) ? 0 : kf + 1;
-                cf = (cf + 1 == C) ? 0 : cf + 1;
+                jf = (jf + 1 == NC) ? 0 : jf + 1;
             };
-            while (pf < ahead && pf < Q) fill();
-            int32_t k = 0, c = 0;
+            while (pf < ahead && pf < P) fill();
+            int32_t k = 0, j = 0;
             uint32_t parity = 0;
-            for (int32_t q = 0; q < Q; ++q) {
+            for (int32_t q = 0; q < P; ++q) {
                 uint32_t spins = 0;
                 bool ok = mbar_try_wait(&empty[k], parity);
                 while (!ok && !abort_flag && ++spins < kWaitLimit) ok = mbar_try_wait(&empty[k], parity);
                 if (!ok) { abort_flag = 1; break; }
-                const int32_t beg = CO[c];
-                bulk_s2g(cs + beg, stages + lay.stage_bytes * (uint32_t)k + lay.arr_bytes,
-                         4u * (uint32_t)(CO[c + 1] - beg));
+                const int32_t beg = CO[j * G];
+                const int32_t end = CO[min(j * G + G, C)];
+                bulk_s2g(cs + beg, stages + lay.stage_bytes * (uint32_t)k + lay.arr_bytes, 4u * (uint32_t)(end - beg));
                 bulk_commit();
-                if (pf < Q) {
+                if (pf < P) {
                     // the stage to refill held position pf - S, stored kStoreSlack steps ago
                     bulk_wait<kStoreGroups>();
                     bulk_wait_read<kStoreSlack>();
                     fill();
                 }
                 if (++k == S) { k = 0; parity ^= 1u; }
-                c = (c + 1 == C) ? 0 : c + 1;
+                j = (j + 1 == NC) ? 0 : j + 1;
             }
             bulk_wait<0>();
             if (abort_flag) atomicOr(err, 1);
@@ -504,10 +506,11 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         return;
     }
     // ---------------- consumers
-    // Thread t updates ranks t, t + nc, ..., t + (E-1) nc of each class: all their loads
-    // are issued before any store (the ends inside a class are distinct).  Warp 0 waits
-    // for the next stage before the class barrier; the barrier (which also ORs the abort
-    // flag) orders that stage's data before every consumer's reads.
+    // Thread t updates ranks t, t + nc, ..., t + (E-1) nc of each class, all loads issued
+    // before any store (the ends inside a class are distinct).  Classes of a chunk are
+    // separated by a consumer barrier; at a chunk's end warp 0 waits for the next stage
+    // and the barrier (which also ORs the abort flag) orders that stage's data before
+    // every consumer's reads.
     auto wait_full = [&](int32_t kk, uint32_t par) -> bool {
         uint32_t spins = 0;
         bool ok = mbar_try_wait(&full[kk], par);
@@ -515,53 +518,58 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         return ok;
     };
     bool bad = false;
-    if (tid < 32 && Q > 0) bad = !wait_full(0, 0);
+    if (tid < 32 && P > 0) bad = !wait_full(0, 0);
     bad = consumer_sync_or(nc, bad);
-    int32_t k = 0, c = 0;
+    int32_t k = 0, j = 0;
     uint32_t parity = 0;
-    int32_t beg = CO[0];
-    for (int32_t q = 0; q < Q && !bad; ++q) {
-        const int32_t end = CO[c + 1];
-        const int32_t len = end - beg;
+    for (int32_t q = 0; q < P && !bad; ++q) {
+        const int32_t c0 = j * G;
+        const int32_t c1 = min(c0 + G, C);
+        const int32_t base = CO[c0];
         unsigned char* st = stages + lay.stage_bytes * (uint32_t)k;
         const uint32_t* suv = reinterpret_cast<const uint32_t*>(st);
         float* ss = reinterpret_cast<float*>(st + lay.arr_bytes);
         const float* sw = reinterpret_cast<const float*>(st + 2 * lay.arr_bytes);
-        for (int32_t r0 = tid; r0 < len; r0 += E * nc) {
-            uint32_t uv[E];
-            EdgeVal e[E];
+        int32_t cb = 0;
+        for (int32_t c = c0; c < c1; ++c) {
+            const int32_t ce = CO[c + 1] - base;
+            for (int32_t r0 = cb + tid; r0 < ce; r0 += E * nc) {
+                uint32_t uv[E];
+                EdgeVal e[E];
 #pragma unroll
-            for (int j = 0; j < E; ++j) {
-                const int32_t r = r0 + j * nc;
-                uv[j] = r < len ? suv[r] : ((uint32_t)n | ((uint32_t)n << 16));
-                e[j].s = r < len ? ss[r] : 0.0f;
-                e[j].w = WEIGHTED ? (r < len ? sw[r] : 0.0f) : 1.0f;
-            }
+                for (int jj = 0; jj < E; ++jj) {
+                    const int32_t r = r0 + jj * nc;
+                    uv[jj] = r < ce ? suv[r] : ((uint32_t)n | ((uint32_t)n << 16));
+                    e[jj].s = r < ce ? ss[r] : 0.0f;
+                    e[jj].w = WEIGHTED ? (r < ce ? sw[r] : 0.0f) : 1.0f;
+                }
 #pragma unroll
-            for (int j = 0; j < E; ++j) {
-                e[j].la = L[end_a(uv[j])];
-                e[j].lb = L[end_b(uv[j])];
-            }
-            float ns[E];
+                for (int jj = 0; jj < E; ++jj) {
+                    e[jj].la = L[end_a(uv[jj])];
+                    e[jj].lb = L[end_b(uv[jj])];
+                }
+                float ns[E];
 #pragma unroll
-            for (int j = 0; j < E; ++j) ns[j] = lowd_transfer(e[j]);
+                for (int jj = 0; jj < E; ++jj) ns[jj] = lowd_transfer(e[jj]);
 #pragma unroll
-            for (int j = 0; j < E; ++j) {
-                const int32_t r = r0 + j * nc;
-                if (r < len) {
-                    L[end_a(uv[j])] = e[j].la;
-                    L[end_b(uv[j])] = e[j].lb;
-                    ss[r] = ns[j];
+                for (int jj = 0; jj < E; ++jj) {
+                    const int32_t r = r0 + jj * nc;
+                    if (r < ce) {
+                        L[end_a(uv[jj])] = e[jj].la;
+                        L[end_b(uv[jj])] = e[jj].lb;
+                        ss[r] = ns[jj];
+                    }
                 }
             }
+            cb = ce;
+            if (c + 1 < c1) consumer_sync(nc);
         }
         fence_proxy_async_smem();
         const int32_t kprev = k;
         if (++k == S) { k = 0; parity ^= 1u; }
-        c = (c + 1 == C) ? 0 : c + 1;
-        beg = end == CO[C] ? 0 : end;
+        j = (j + 1 == NC) ? 0 : j + 1;
         bool fail = false;
-        if (tid < 32 && q + 1 < Q) fail = !wait_full(k, parity);
+        if (tid < 32 && q + 1 < P) fail = !wait_full(k, parity);
         bad = consumer_sync_or(nc, fail);
         if (tid == 0) mbar_arrive(&empty[kprev]);
     }
@@ -600,15 +608,24 @@ template <bool WEIGHTED>
 cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* launched) {
     *launched = false;
     const size_t budget = 227 * 1024;
-    int32_t S = kTmaMaxStages;
-    TmaLayout lay = tma_layout(h->n, h->C, S, maxlen, WEIGHTED);
-    while (S > 3 && lay.total > budget) {
-        --S;
-        lay = tma_layout(h->n, h->C, S, maxlen, WEIGHTED);
+    // chunk size G (classes per staged copy) and stage count S: the largest G whose
+    // chunks leave room for at least kMinStages stages, then as many stages as fit
+    constexpr int kMinStages = 5;
+    int32_t G = 0, S = 0, chunk = 0;
+    TmaLayout lay{};
+    for (int32_t g : {8, 4, 2, 1}) {
+        int32_t mx = 0;  // longest chunk of g classes
+        for (int32_t c0 = 0; c0 < h->C; c0 += g) mx = max(mx, h->coff_h[min(c0 + g, h->C)] - h->coff_h[c0]);
+        int32_t s = kTmaMaxStages;
+        TmaLayout t = tma_layout(h->n, h->C, s, mx, WEIGHTED);
+        while (s > kMinStages && t.total > budget) t = tma_layout(h->n, h->C, --s, mx, WEIGHTED);
+        if (t.total <= budget) { G = g; S = s; chunk = mx; lay = t; break; }
     }
-    // a class's splits are re-read one pass later: its store must be older than the
+    if (G == 0) return cudaSuccess;
+    const int32_t NC = (h->C + G - 1) / G;
+    // a chunk's splits are re-read one pass later: its store must be older than the
     // kStoreGroups stores allowed in flight when the producer loads it again
-    if (lay.total > budget || S - kStoreSlack < 2 || h->C < S - kStoreSlack + kStoreGroups + 1) return cudaSuccess;
+    if (NC < S - kStoreSlack + kStoreGroups + 1) return cudaSuccess;
     // edges per consumer thread: enough warps to hide latency, few enough to keep the
     // per-class bookkeeping small
     const int E = maxlen > 2048 ? 4 : (maxlen > 512 ? 2 : 1);
@@ -618,10 +635,16 @@ cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* 
     auto kern = E == 4 ? k_sweep_tma<WEIGHTED, 4> : (E == 2 ? k_sweep_tma<WEIGHTED, 2> : k_sweep_tma<WEIGHTED, 1>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
     if (e != cudaSuccess) return e;
-    LOWD_LAUNCH(kern, 1, threads + 32, lay.total, h->st, h->n, h->C, h->coff, h->cuv, h->cw, h->cs, h->l, passes,
-                S, maxlen, h->d_i32 + 8);
+    const int32_t per = (int32_t)(0x7fffffff / NC);
+    for (int32_t done = 0; done < passes && e == cudaSuccess;) {
+        const int32_t k = passes - done < per ? passes - done : per;
+        LOWD_LAUNCH(kern, 1, threads + 32, lay.total, h->st, h->n, h->C, h->coff, h->cuv, h->cw, h->cs, h->l, k,
+                    S, G, chunk, h->d_i32 + 8);
+        e = cudaGetLastError();
+        done += k;
+    }
     *launched = true;
-    return cudaGetLastError();
+    return e;
 }
 
 template <bool WEIGHTED>
@@ -665,14 +688,7 @@ cudaError_t run_passes(lowd_ctx* h, int32_t passes) {
     if (passes <= 0 || h->m == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(h->d_i32 + 8, 0, sizeof(int32_t), h->st);
     if (e != cudaSuccess) return e;
-    // one launch covers at most 2^31 - 1 class updates
-    const int32_t per = (int32_t)(0x7fffffff / (h->C > 0 ? h->C : 1));
-    for (int32_t done = 0; done < passes && e == cudaSuccess;) {
-        const int32_t k = passes - done < per ? passes - done : per;
-        e = h->cw ? launch_sweep<true>(h, k) : launch_sweep<false>(h, k);
-        done += k;
-    }
-    return e;
+    return h->cw ? launch_sweep<true>(h, passes) : launch_sweep<false>(h, passes);
 }
 
 }  // namespace
