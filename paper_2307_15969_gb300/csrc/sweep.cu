@@ -36,23 +36,48 @@ inline unsigned grid_for(int64_t n) {
     return (unsigned)b;
 }
 
+// Colour of each edge (the circle colouring) and its place inside the class.  Inside a
+// class every edge pairs a and b = c - a (mod P); with b < P the high end is fixed by the
+// low one and the wrap group g = [a + b >= P], so edges of one group whose low ends lie
+// in distinct shared-memory banks (a mod 32) also have high ends in distinct banks.  The
+// first key orders a class by (group, bank of the low end); the second deals the edges
+// out bank by bank in rounds, so consecutive edges (one warp's accesses) mostly touch
+// 32 different banks at both ends.
+constexpr int kRankBits = 16;  // rank inside a (class, group, bank) bucket: < 2^16
+
 __global__ void k_circle_colour(const int32_t* __restrict__ u, const int32_t* __restrict__ v, int64_t m,
-                                int32_t n, uint32_t* __restrict__ key, int32_t* __restrict__ val) {
+                                int32_t n, uint64_t* __restrict__ key, int32_t* __restrict__ val) {
     const uint32_t Np = (uint32_t)(n + (n & 1));
     const uint32_t P = Np - 1;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t a = (uint32_t)u[e], b = (uint32_t)v[e];
-        uint32_t c = (b == Np - 1) ? (2u * a) % P : (a + b) % P;
-        key[e] = c;
+        const uint32_t a = (uint32_t)u[e], b = (uint32_t)v[e];
+        const uint32_t c = (b == Np - 1) ? (2u * a) % P : (a + b) % P;
+        const uint32_t g = (b != Np - 1 && a + b >= P) ? 1u : 0u;
+        key[e] = ((uint64_t)c << 6) | ((uint64_t)g << 5) | (uint64_t)(a & 31u);
         val[e] = (int32_t)e;
     }
 }
 
-__global__ void k_class_heads(const uint32_t* __restrict__ key, int64_t m, int32_t* __restrict__ head) {
+// Second key: (colour, group, rank inside its (colour, group, bank) bucket, bank).
+__global__ void k_bank_rounds(const uint64_t* __restrict__ key, int64_t m, uint64_t* __restrict__ key2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = key[i];
+        int64_t lo = 0, hi = i;  // first index with key == k
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (key[mid] < k) lo = mid + 1; else hi = mid;
+        }
+        const uint64_t r = (uint64_t)(i - lo);
+        key2[i] = ((k >> 5) << (kRankBits + 5)) | (r << 5) | (k & 31u);
+    }
+}
+
+__global__ void k_class_heads(const uint64_t* __restrict__ key, int64_t m, int shift, int32_t* __restrict__ head) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x)
-        head[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+        head[i] = (i == 0 || (key[i] >> shift) != (key[i - 1] >> shift)) ? 1 : 0;
 }
 
 __global__ void k_class_offsets(const int32_t* __restrict__ head, const int32_t* __restrict__ hpos,
@@ -708,7 +733,7 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
                  n, LOWD_SMEM_NODES);
         return LOWD_ERR_TOO_LARGE;
     }
-    uint32_t* key[2] = {nullptr, nullptr};
+    uint64_t* key[2] = {nullptr, nullptr};
     int32_t* val[2] = {nullptr, nullptr};
     int32_t *head = nullptr, *hpos = nullptr, *pcnt = nullptr;
     lowd_status s = LOWD_OK;
@@ -726,13 +751,22 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
         if ((s = dalloc(h, &hpos, m))) break;
         int32_t C = 0;
         int cur = 0;
+        uint64_t* kfin = key[0];
+        int32_t* vfin = val[0];
         if (m > 0) {
             LOWD_LAUNCH(k_circle_colour, grid_for(m), kT, 0, st, h->u, h->v, m, n, key[0], val[0]);
             const uint32_t P = (uint32_t)(n + (n & 1)) - 1u;
-            int bits = bit_length_u64(P > 0 ? P - 1 : 0);
-            if (bits < 1) bits = 1;
-            cur = radix_sort_pairs<uint32_t, int32_t>(key[0], val[0], key[1], val[1], m, bits, h->tmp, st);
-            LOWD_LAUNCH(k_class_heads, grid_for(m), kT, 0, st, key[cur], m, head);
+            const int cbits = bit_length_u64(P > 0 ? P - 1 : 0);
+            cur = radix_sort_pairs<uint64_t, int32_t>(key[0], val[0], key[1], val[1], m, cbits + 6, h->tmp, st);
+            uint64_t* kA = key[cur];
+            int32_t* vA = val[cur];
+            uint64_t* kB = key[1 - cur];
+            int32_t* vB = val[1 - cur];
+            LOWD_LAUNCH(k_bank_rounds, grid_for(m), kT, 0, st, kA, m, kB);
+            const int r2 = radix_sort_pairs<uint64_t, int32_t>(kB, vA, kA, vB, m, cbits + 6 + kRankBits, h->tmp, st);
+            kfin = r2 ? kA : kB;
+            vfin = r2 ? vB : vA;
+            LOWD_LAUNCH(k_class_heads, grid_for(m), kT, 0, st, kfin, m, kRankBits + 6, head);
             scan_exclusive<int32_t>(head, hpos, m, h->d_i32 + 5, h->tmp, st);
             if (cudaMemcpyAsync(h->h_pin, h->d_i32 + 5, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                 cudaStreamSynchronize(st) != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
@@ -760,7 +794,7 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
         if ((s = dalloc(h, &h->perm, m_pad))) break;
         if (m_pad > 0) LOWD_LAUNCH(k_fill_perm, grid_for(m_pad), kT, 0, st, h->perm, m_pad);
         if (m > 0)
-            LOWD_LAUNCH(k_scatter_padded, grid_for(m), kT, 0, st, val[cur], head, hpos, h->coff_real, h->coff, m,
+            LOWD_LAUNCH(k_scatter_padded, grid_for(m), kT, 0, st, vfin, head, hpos, h->coff_real, h->coff, m,
                         h->perm);
         if ((s = dalloc(h, &h->cuv, m_pad))) break;
         if (h->w && (s = dalloc(h, &h->cw, m_pad))) break;
