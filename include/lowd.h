@@ -203,6 +203,32 @@ lowd_status lowd_get_prune_info(lowd_handle h, int32_t* sort_perm, int32_t* remo
 lowd_status lowd_get_edge_order(lowd_handle h, int32_t* perm, int32_t* class_offsets,
                                 int32_t* classes);
 
+/*
+ * lowd_extract_noalloc - the extraction of lowd_extract on caller-provided DEVICE arrays,
+ * without any device allocation.  The paper has no counterpart: this is a service for
+ * callers that cannot let a library allocate device memory - for example a process whose
+ * device memory belongs to its own pool allocator, or a loop with a fixed memory budget
+ * that cannot absorb the device-wide synchronisation cudaMalloc/cudaFree may cause.
+ *   n, m       nodes (1 <= n <= 65536) and edges (0 <= m < 2^31)
+ *   u, v       device int32 [m]: edge ends, each pair listed once, ids in [0, n)
+ *   w          device float [m] weights, or NULL for unit weights; each weight counts as
+ *              its nearest multiple of 2^-20 (at least 2^-20), as in lowd_load_graph
+ *   loads      device float [n]: node loads (e.g. from lowd_get_loads)
+ *   S          device int32 [n] out: ids of S* ascending, or NULL
+ *   S_size     host out: |S*|;   rho   host out: W(S*)/|S*|
+ *   stream     cudaStream_t (as void*); the call synchronises it before returning
+ * Returns LOWD_ERR_TOO_LARGE when n > 65536 and LOWD_ERR_INVALID_ARG on bad arguments.
+ * All intermediate buffers come from one static device array of 4 MiB that every GPU
+ * which loads this library holds until the process exits.  Its device address is looked
+ * up (cudaGetSymbolAddress) on the first call made on each device, with that device
+ * current; make that first call before capturing any stream.  The array is shared by all
+ * calls and keeps the previous call's contents, so calls that overlap on the GPU (other
+ * streams, other host threads) race with each other: serialise them.
+ */
+lowd_status lowd_extract_noalloc(int32_t n, int64_t m, const int32_t* u, const int32_t* v,
+                                 const float* w, const float* loads, int32_t* S, int32_t* S_size,
+                                 double* rho, void* stream);
+
 /* Release the handle and all its device memory.  NULL is ignored. */
 void lowd_free(lowd_handle h);
 

@@ -13,6 +13,9 @@
 // in shared memory (4 bytes each) for the whole sweep.
 #define LOWD_SMEM_NODES 53248
 
+// Largest graph (nodes) lowd_extract_noalloc accepts.
+#define LOWD_NOALLOC_MAX_NODES 65536
+
 struct lowd_ctx {
     cudaStream_t st = nullptr;
     int mem = LOWD_MEM_HOST;

@@ -178,3 +178,147 @@ lowd_status lowd_extract_best(lowd_ctx* h, const float* loads_dev, int32_t* S_de
     cleanup();
     return s;
 }
+
+// ------------------------------------------------------------------ allocation-free variant
+//
+// lowd_extract_noalloc runs the same extraction kernels as lowd_extract on arrays the
+// caller passes, taking every intermediate buffer from one statically sized device array
+// instead of cudaMalloc.  It serves callers that must not allocate device memory
+// themselves or through the library: a process whose device memory is owned by its own
+// pool allocator, or a loop with a fixed memory budget that cannot afford the implicit
+// device synchronisation of cudaMalloc/cudaFree.  The array lives for the life of the
+// process on every device that loads this library, so its size is kept small: graphs of
+// at most LOWD_NOALLOC_MAX_NODES nodes.
+
+#include <mutex>
+
+namespace {
+
+constexpr int32_t kNoallocMaxNodes = LOWD_NOALLOC_MAX_NODES;
+constexpr int kNoallocMaxDevices = 64;
+
+inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// carve-up of the scratch array for n nodes (byte offsets, each 256-aligned)
+struct NoallocLayout {
+    size_t key0, key1, val0, val1, pos, bucket, excl, flag, fpos, part, tmp, total;
+};
+
+constexpr size_t noalloc_part_entries() {
+    return (size_t)((kNoallocMaxNodes + 255) / 256) + 1;
+}
+
+inline NoallocLayout noalloc_layout(int32_t n) {
+    NoallocLayout L{};
+    size_t o = 0;
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    L.key0 = o; o = al256(o + 4 * nn);
+    L.key1 = o; o = al256(o + 4 * nn);
+    L.val0 = o; o = al256(o + 4 * nn);
+    L.val1 = o; o = al256(o + 4 * nn);
+    L.pos = o; o = al256(o + 4 * nn);
+    L.bucket = o; o = al256(o + 8 * nn);
+    L.excl = o; o = al256(o + 8 * nn);
+    L.flag = o; o = al256(o + 4 * nn);
+    L.fpos = o; o = al256(o + 4 * nn);
+    L.part = o; o = al256(o + sizeof(Best) * noalloc_part_entries());
+    L.tmp = o; o = al256(o + lowd_sort_tmp_bytes(n));
+    L.total = o;
+    return L;
+}
+
+// The scratch, sized for the largest graph accepted: for LOWD_NOALLOC_MAX_NODES nodes the
+// carve-up needs about 2.8 MiB; each call checks the carve-up against this size.
+constexpr size_t kNoallocScratchBytes = (size_t)4 << 20;  // 4 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+
+// Device address of the scratch on the current device, looked up once per device.
+cudaError_t noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+// weight of each edge in 2^-20 units, rounded as lowd_load_graph rounds it
+__global__ void k_edge_buckets_f32(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                                   const float* __restrict__ w, int64_t m, const int32_t* __restrict__ pos,
+                                   unsigned long long* __restrict__ bucket) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = max(pos[u[e]], pos[v[e]]);
+        unsigned long long x = 1ull;
+        if (w) {
+            const double y = rint((double)w[e] * 1048576.0);
+            x = y < 1.0 ? 1ull : (unsigned long long)y;
+        }
+        atomicAdd(&bucket[p], x);
+    }
+}
+
+}  // namespace
+
+extern "C" lowd_status lowd_extract_noalloc(int32_t n, int64_t m, const int32_t* u, const int32_t* v,
+                                            const float* w, const float* loads, int32_t* S, int32_t* S_size,
+                                            double* rho, void* stream) {
+    if (n < 1 || m < 0 || m >= ((int64_t)1 << 31) || !loads || (m > 0 && (!u || !v)) || !S_size || !rho)
+        return LOWD_ERR_INVALID_ARG;
+    if (n > kNoallocMaxNodes) return LOWD_ERR_TOO_LARGE;
+    const NoallocLayout lay = noalloc_layout(n);
+    if (lay.total > kNoallocScratchBytes) return LOWD_ERR_TOO_LARGE;
+    void* base = nullptr;
+    if (noalloc_scratch(&base) != cudaSuccess) {
+        cudaGetLastError();
+        return LOWD_ERR_CUDA;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* b = (unsigned char*)base;
+    uint32_t* key0 = (uint32_t*)(b + lay.key0);
+    uint32_t* key1 = (uint32_t*)(b + lay.key1);
+    int32_t* val0 = (int32_t*)(b + lay.val0);
+    int32_t* val1 = (int32_t*)(b + lay.val1);
+    int32_t* pos = (int32_t*)(b + lay.pos);
+    unsigned long long* bucket = (unsigned long long*)(b + lay.bucket);
+    int64_t* excl = (int64_t*)(b + lay.excl);
+    int32_t* flag = (int32_t*)(b + lay.flag);
+    int32_t* fpos = (int32_t*)(b + lay.fpos);
+    Best* part = (Best*)(b + lay.part);
+    void* tmp = b + lay.tmp;
+    const unsigned nb = grid_for(n);
+    // the array keeps the previous call's contents: the buckets must start at zero
+    cudaMemsetAsync(bucket, 0, sizeof(unsigned long long) * (size_t)n, st);
+    LOWD_LAUNCH(k_load_keys, grid_for(n), kT, 0, st, loads, n, key0, val0);
+    const int cur = radix_sort_pairs<uint32_t, int32_t>(key0, val0, key1, val1, n, 32, tmp, st);
+    LOWD_LAUNCH(k_positions, grid_for(n), kT, 0, st, cur ? val1 : val0, n, pos);
+    if (m > 0) LOWD_LAUNCH(k_edge_buckets_f32, grid_for(m), kT, 0, st, u, v, w, m, pos, bucket);
+    scan_exclusive<int64_t>((const int64_t*)bucket, excl, n, nullptr, tmp, st);
+    LOWD_LAUNCH(k_best_prefix, nb, kT, 0, st, excl, bucket, n, part);
+    LOWD_LAUNCH(k_best_final, 1, 32, 0, st, part, (int32_t)nb, part + nb);
+    LOWD_LAUNCH(k_in_best, grid_for(n), kT, 0, st, pos, n, part + nb, flag);
+    scan_exclusive<int32_t>(flag, fpos, n, nullptr, tmp, st);
+    if (S) LOWD_LAUNCH(k_emit_members, grid_for(n), kT, 0, st, flag, fpos, n, nullptr, S);
+    Best best;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&best, part + nb, sizeof(Best), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LOWD_ERR_CUDA;
+    }
+    *S_size = (int32_t)best.k;
+    const double scale = w ? 1048576.0 : 1.0;
+    *rho = best.k > 0 ? (double)best.W / scale / (double)best.k : 0.0;
+    return LOWD_OK;
+}

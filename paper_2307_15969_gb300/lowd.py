@@ -33,7 +33,7 @@ EXPORTED = (
     "lowd_load_graph", "lowd_prune", "lowd_iterate", "lowd_extract", "lowd_get_info",
     "lowd_get_graph", "lowd_get_splits", "lowd_set_splits", "lowd_get_loads",
     "lowd_get_prune_info", "lowd_get_edge_order", "lowd_free", "lowd_status_string",
-    "lowd_last_error", "lowd_launch_count",
+    "lowd_last_error", "lowd_launch_count", "lowd_extract_noalloc",
 )
 
 
@@ -106,6 +106,8 @@ def load_library(path: str = LIB_PATH):
     lib.lowd_last_error.argtypes = [P]
     lib.lowd_launch_count.restype = C.c_uint64
     lib.lowd_launch_count.argtypes = []
+    lib.lowd_extract_noalloc.restype = i32
+    lib.lowd_extract_noalloc.argtypes = [i32, i64, P, P, P, P, P, C.POINTER(i32), C.POINTER(C.c_double), P]
     _lib = lib
     return lib
 
@@ -282,6 +284,21 @@ def lowd_get_edge_order(h: Handle):
     h._check(load_library().lowd_get_edge_order(h.ptr, h.ptr_of(perm), h.ptr_of(offs), C.byref(c)),
              "lowd_get_edge_order")
     return perm[:info["m"]], offs[:c.value + 1]
+
+
+def lowd_extract_noalloc(n: int, u, v, w, loads, S=None, stream=None):
+    """Allocation-free extraction on CUDA tensors (see include/lowd.h).  Returns
+    (status, |S*|, rho*); S (int32 CUDA tensor of >= n entries) receives S* if given."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    k = C.c_int32()
+    rho = C.c_double()
+
+    def p(t):
+        return None if t is None else C.c_void_p(t.data_ptr())
+    s = load_library().lowd_extract_noalloc(int(n), int(u.numel()), p(u), p(v), p(w), p(loads), p(S),
+                                            C.byref(k), C.byref(rho), C.c_void_p(st.cuda_stream))
+    return s, k.value, rho.value
 
 
 def lowd_free(h: Handle):
