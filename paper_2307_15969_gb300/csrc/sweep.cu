@@ -101,20 +101,15 @@ __global__ void k_fill_perm(int32_t* __restrict__ perm_pad, int64_t m_pad) {
         perm_pad[i] = -1;
 }
 
-// Real position i (class-major, unpadded) -> padded, interleaved position.
+// Real position i (class-major, unpadded) -> padded position.
 __global__ void k_scatter_padded(const int32_t* __restrict__ perm, const int32_t* __restrict__ head,
                                  const int32_t* __restrict__ hpos, const int32_t* __restrict__ coff_real,
                                  const int32_t* __restrict__ coff_pad, int64_t m,
                                  int32_t* __restrict__ perm_pad) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
-        // rank r of the class goes to component r / V of 16-byte vector r % V (V vectors in
-        // the padded class): lane t of a warp then holds ranks t, V + t, 2V + t, 3V + t,
-        // which the bank-aware order places in distinct banks
         const int32_t c = hpos[i] + head[i] - 1;
-        const int32_t r = (int32_t)(i - coff_real[c]);
-        const int32_t V = (coff_pad[c + 1] - coff_pad[c]) >> 2;
-        perm_pad[coff_pad[c] + 4 * (r % V) + r / V] = perm[i];
+        perm_pad[coff_pad[c] + (i - coff_real[c])] = perm[i];
     }
 }
 
@@ -549,11 +544,11 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         return;
     }
     // ---------------- consumers
-    // Thread t updates 16-byte vector t of each class (4 edges: ranks t, V+t, 2V+t, 3V+t),
-    // all loads issued before any store (the ends inside a class are distinct).  Classes
-    // of a chunk are separated by a consumer barrier; at a chunk's end warp 0 waits for
-    // the next stage and the barrier (which also ORs the abort flag) orders that stage's
-    // data before every consumer's reads.
+    // Thread t updates ranks t, t + nc, ..., t + (E-1) nc of each class, all loads issued
+    // before any store (the ends inside a class are distinct).  Classes of a chunk are
+    // separated by a consumer barrier; at a chunk's end warp 0 waits for the next stage
+    // and the barrier (which also ORs the abort flag) orders that stage's data before
+    // every consumer's reads.
     auto wait_full = [&](int32_t kk, uint32_t par) -> bool {
         uint32_t spins = 0;
         bool ok = mbar_try_wait(&full[kk], par);
@@ -570,17 +565,41 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         const int32_t c1 = min(c0 + G, C);
         const int32_t base = CO[c0];
         unsigned char* st = stages + lay.stage_bytes * (uint32_t)k;
-        const uint4* suv = reinterpret_cast<const uint4*>(st);
-        float4* ss = reinterpret_cast<float4*>(st + lay.arr_bytes);
-        const float4* sw = reinterpret_cast<const float4*>(st + 2 * lay.arr_bytes);
-        int32_t vb = 0;  // first vector of class c inside the stage
+        const uint32_t* suv = reinterpret_cast<const uint32_t*>(st);
+        float* ss = reinterpret_cast<float*>(st + lay.arr_bytes);
+        const float* sw = reinterpret_cast<const float*>(st + 2 * lay.arr_bytes);
+        int32_t cb = 0;
         for (int32_t c = c0; c < c1; ++c) {
-            const int32_t ve = (CO[c + 1] - base) >> 2;
-            for (int32_t i = vb + tid; i < ve; i += nc) {
-                const float4 w4 = WEIGHTED ? sw[i] : float4{1.f, 1.f, 1.f, 1.f};
-                ss[i] = update4<WEIGHTED>(L, suv[i], ss[i], w4);
+            const int32_t ce = CO[c + 1] - base;
+            for (int32_t r0 = cb + tid; r0 < ce; r0 += E * nc) {
+                uint32_t uv[E];
+                EdgeVal e[E];
+#pragma unroll
+                for (int jj = 0; jj < E; ++jj) {
+                    const int32_t r = r0 + jj * nc;
+                    uv[jj] = r < ce ? suv[r] : ((uint32_t)n | ((uint32_t)n << 16));
+                    e[jj].s = r < ce ? ss[r] : 0.0f;
+                    e[jj].w = WEIGHTED ? (r < ce ? sw[r] : 0.0f) : 1.0f;
+                }
+#pragma unroll
+                for (int jj = 0; jj < E; ++jj) {
+                    e[jj].la = L[end_a(uv[jj])];
+                    e[jj].lb = L[end_b(uv[jj])];
+                }
+                float ns[E];
+#pragma unroll
+                for (int jj = 0; jj < E; ++jj) ns[jj] = lowd_transfer(e[jj]);
+#pragma unroll
+                for (int jj = 0; jj < E; ++jj) {
+                    const int32_t r = r0 + jj * nc;
+                    if (r < ce) {
+                        L[end_a(uv[jj])] = e[jj].la;
+                        L[end_b(uv[jj])] = e[jj].lb;
+                        ss[r] = ns[jj];
+                    }
+                }
             }
-            vb = ve;
+            cb = ce;
             if (c + 1 < c1) consumer_sync(nc);
         }
         fence_proxy_async_smem();
@@ -645,11 +664,13 @@ cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* 
     // a chunk's splits are re-read one pass later: its store must be older than the
     // kStoreGroups stores allowed in flight when the producer loads it again
     if (NC < S - kStoreSlack + kStoreGroups + 1) return cudaSuccess;
-    // one consumer thread per 16-byte vector (4 edges) of the largest class
-    int threads = ((((maxlen >> 2) + 31) / 32) * 32);
+    // edges per consumer thread: enough warps to hide latency, few enough to keep the
+    // per-class bookkeeping small
+    const int E = maxlen > 2048 ? 4 : (maxlen > 512 ? 2 : 1);
+    int threads = ((((maxlen + E - 1) / E) + 31) / 32) * 32;
     if (threads < 64) threads = 64;
     if (threads > kTmaConsumers) threads = kTmaConsumers;
-    auto kern = k_sweep_tma<WEIGHTED, 4>;
+    auto kern = E == 4 ? k_sweep_tma<WEIGHTED, 4> : (E == 2 ? k_sweep_tma<WEIGHTED, 2> : k_sweep_tma<WEIGHTED, 1>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
     if (e != cudaSuccess) return e;
     const int32_t per = (int32_t)(0x7fffffff / NC);
