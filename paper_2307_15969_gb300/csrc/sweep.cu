@@ -427,7 +427,7 @@ __device__ __forceinline__ void fence_mbar_init() {
 
 constexpr int kTmaConsumers = 992;   // one edge per consumer thread per class
 constexpr int kTmaMaxStages = 16;
-constexpr int kStoreSlack = 2;    // bulk stores allowed to be still reading their stage
+constexpr int kStoreSlack = 1;    // bulk stores allowed to be still reading their stage
 constexpr int kStoreGroups = 8;   // bulk stores allowed in flight at all
 constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait rounds before giving up
 
@@ -648,10 +648,10 @@ cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* 
     const size_t budget = 227 * 1024;
     // chunk size G (classes per staged copy) and stage count S: the largest G whose
     // chunks leave room for at least kMinStages stages, then as many stages as fit
-    constexpr int kMinStages = 5;
+    constexpr int kMinStages = 3;
     int32_t G = 0, S = 0, chunk = 0;
     TmaLayout lay{};
-    for (int32_t g : {8, 4, 2, 1}) {
+    for (int32_t g : {16, 8, 4, 2, 1}) {
         int32_t mx = 0;  // longest chunk of g classes
         for (int32_t c0 = 0; c0 < h->C; c0 += g) mx = max(mx, h->coff_h[min(c0 + g, h->C)] - h->coff_h[c0]);
         int32_t s = kTmaMaxStages;
@@ -666,7 +666,7 @@ cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* 
     if (NC < S - kStoreSlack + kStoreGroups + 1) return cudaSuccess;
     // edges per consumer thread: enough warps to hide latency, few enough to keep the
     // per-class bookkeeping small
-    const int E = maxlen > 2048 ? 4 : (maxlen > 512 ? 2 : 1);
+    const int E = maxlen > 2 * kTmaConsumers ? 4 : (maxlen > kTmaConsumers ? 2 : 1);
     int threads = ((((maxlen + E - 1) / E) + 31) / 32) * 32;
     if (threads < 64) threads = 64;
     if (threads > kTmaConsumers) threads = kTmaConsumers;
