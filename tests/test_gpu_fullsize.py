@@ -1,0 +1,77 @@
+"""GPU parity at the full size of the benchmark workload (R-MAT scale 22, 67.1 M edges),
+through the same calls and launch configuration `bench.py` times.
+
+Checked against the oracle: the counting-sort order and the removal round of all 4.19 M
+nodes, and the 6.49 M edges of the pruned core H (bit-exact); two same-order LOWD passes
+replayed by the FP64 oracle on H (loads within the FP32 tolerance); the extraction on the
+GPU's loads (bit-exact).  Properties that hold at any size: conservation of the total
+weight, non-increasing sum of squared loads, splits inside [0, w], and weak duality
+rho(S) <= D.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+LOAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def setup():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_15969_gb300 import build
+    build.build()
+    import paper_2307_15969_gb300 as pkg
+    import oracle
+    oracle.build()
+    g = synth.workload("rmat22")
+    return torch, pkg, oracle, g
+
+
+def test_rmat22_prune_core_and_passes(setup):
+    torch, pkg, orc, g = setup
+    h = pkg.lowd_load_graph(g.n, torch.from_numpy(g.u).cuda(), torch.from_numpy(g.v).cuda())
+    info0 = pkg.lowd_get_info(h)
+    assert info0["m"] == g.m and info0["duplicates"] == 0
+    nk, mk, rounds = pkg.lowd_prune(h)
+    # oracle pruning on the full graph
+    wu = np.ones(g.m, np.int64)
+    deg = orc.degrees(g.n, g.u, g.v, wu)
+    pr = orc.prune(g.n, g.u, g.v, wu, False)
+    perm, rr = pkg.lowd_get_prune_info(h)
+    assert np.array_equal(perm.cpu().numpy(), orc.degree_order(deg, False))
+    assert np.array_equal(rr.cpu().numpy(), pr["removal_round"])
+    assert rounds == pr["rounds"]
+    keep = pr["removal_round"] < 0
+    nh, uh, vh, _, _ = orc.compact(g.n, g.u, g.v, None, keep)
+    gu, gv, _ = pkg.lowd_get_graph(h)
+    gu, gv = gu.cpu().numpy(), gv.cpu().numpy()
+    assert (nk, mk) == (nh, uh.shape[0])
+    assert np.array_equal(gu, uh) and np.array_equal(gv, vh)
+
+    # two passes, replayed in the GPU's order by the FP64 oracle
+    st1 = pkg.lowd_iterate(h, 1)
+    order = pkg.lowd_get_edge_order(h)[0].cpu().numpy()
+    st2 = pkg.lowd_iterate(h, 1)
+    o = orc.LowdState(nh, uh, vh)
+    o.iterate(2, order=order)
+    lg = pkg.lowd_get_loads(h).cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(lg - o.l)) <= LOAD_TOL * o.l.max()
+    # properties: conservation, monotone sum of squares, box
+    assert abs(st2["sum_load"] - mk) <= 1e-6 * mk
+    assert st2["sum_load_sq"] <= st1["sum_load_sq"] * (1 + 1e-9)
+    s = pkg.lowd_get_splits(h).cpu().numpy()
+    assert np.all(s >= 0) and np.all(s <= 1)
+
+    # extraction: bit-exact against the oracle on the GPU's loads; weak duality
+    S, rho, _ = pkg.lowd_extract(h, want_loads=False)
+    So, Wo = orc.extract(nh, uh, vh, np.ones(uh.shape[0], np.int64), lg)
+    idmap = np.nonzero(keep)[0]
+    assert np.array_equal(S.cpu().numpy(), idmap[So])
+    assert rho == Wo / So.shape[0]
+    assert rho <= st2["max_load"] * (1 + 1e-12)
+    pkg.lowd_free(h)
