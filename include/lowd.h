@@ -229,6 +229,57 @@ lowd_status lowd_extract_noalloc(int32_t n, int64_t m, const int32_t* u, const i
                                  const float* w, const float* loads, int32_t* S, int32_t* S_size,
                                  double* rho, void* stream);
 
+/* ------------------------------------------------------------------ batched graphs
+ *
+ * Many independent graphs through the whole method (Algorithm 2, colouring, Algorithm 1
+ * passes, extraction) in one persistent kernel launch, replayed from a captured CUDA
+ * graph.  Each CTA takes graphs from a work queue and runs one graph at a time with its
+ * node state in shared memory.  Unit weights only.
+ */
+typedef struct lowd_batch_ctx* lowd_batch;
+
+enum { LOWD_BATCH_ORDER_AS_GIVEN = 1, LOWD_BATCH_ORDER_LARGEST_FIRST = 2 };
+
+/* Launch schedule of lowd_batch_run; zero fields take the autotuned (or default) value. */
+typedef struct {
+    int32_t passes;       /* LOWD passes per graph (>= 0) */
+    int32_t ctas_per_sm;  /* 1 or 2 (shared memory is split between them) */
+    int32_t threads;      /* threads per CTA: multiple of 32 in [64, 1024] */
+    int32_t order;        /* LOWD_BATCH_ORDER_* : order in which graphs enter the queue */
+} lowd_batch_options;
+
+/*
+ * lowd_batch_create - copy a batch of B graphs and check it.
+ *   node_off [B+1], edge_off [B+1]  prefix offsets (node_off[0] = edge_off[0] = 0), host
+ *                                   or device per `mem`; every graph has >= 1 node
+ *   u, v [edge_off[B]]             local node ids of each graph's edges: u < v < n_g and
+ *                                   strictly increasing (u, v) inside a graph (the canonical
+ *                                   form of Sec. IV: no loops, no repeats)
+ * Graphs whose node count exceeds the kernel's shared-memory budget (about 45,000 nodes
+ * at one CTA per SM) are reported with status 1 by lowd_batch_results instead of a result.
+ */
+lowd_status lowd_batch_create(int32_t B, const int64_t* node_off, const int64_t* edge_off,
+                              const int32_t* u, const int32_t* v, int32_t mem, void* stream,
+                              lowd_batch* out);
+
+/* Run the method on every graph (Algorithm 2, then Algorithm 1 with opt->passes passes,
+ * then the extraction).  The first run with a given schedule captures it in a CUDA graph;
+ * later runs replay it.  Synchronises the stream. */
+lowd_status lowd_batch_run(lowd_batch b, const lowd_batch_options* opt);
+
+/* Time every schedule (graph order x CTAs per SM x threads) on a spread sample of `sample`
+ * graphs (0 = all) at `passes` passes; keep the fastest as the default and return it. */
+lowd_status lowd_batch_autotune(lowd_batch b, int32_t passes, int32_t sample, lowd_batch_options* best);
+
+/* Per-graph results of the last run, all arrays optional, host or device per `mem`:
+ * rho [B] (W(S*)/|S*|), S_size [B], in_S [node_off[B]] (1 if the node is in S*, by local
+ * id), n_core / m_core [B] (size of the pruned graph), rounds [B] (pruning rounds),
+ * status [B] (0 ok, 1 too many nodes, 2 pruned core too large for the extraction). */
+lowd_status lowd_batch_results(lowd_batch b, double* rho, int32_t* S_size, uint8_t* in_S,
+                               int32_t* n_core, int32_t* m_core, int32_t* rounds, int32_t* status);
+
+void lowd_batch_free(lowd_batch b);
+
 /* Release the handle and all its device memory.  NULL is ignored. */
 void lowd_free(lowd_handle h);
 

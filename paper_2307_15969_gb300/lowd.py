@@ -34,7 +34,11 @@ EXPORTED = (
     "lowd_get_graph", "lowd_get_splits", "lowd_set_splits", "lowd_get_loads",
     "lowd_get_prune_info", "lowd_get_edge_order", "lowd_free", "lowd_status_string",
     "lowd_last_error", "lowd_launch_count", "lowd_extract_noalloc",
+    "lowd_batch_create", "lowd_batch_run", "lowd_batch_autotune", "lowd_batch_results",
+    "lowd_batch_free",
 )
+LOWD_BATCH_ORDER_AS_GIVEN = 1
+LOWD_BATCH_ORDER_LARGEST_FIRST = 2
 
 
 class lowd_options(C.Structure):
@@ -53,6 +57,11 @@ class lowd_info(C.Structure):
                 ("duplicates", C.c_int64), ("weighted", C.c_int32), ("pruned", C.c_int32),
                 ("classes", C.c_int32), ("schedule", C.c_int32), ("max_degree", C.c_int32),
                 ("prune_rounds", C.c_int32)]
+
+
+class lowd_batch_options(C.Structure):
+    _fields_ = [("passes", C.c_int32), ("ctas_per_sm", C.c_int32), ("threads", C.c_int32),
+                ("order", C.c_int32)]
 
 
 class LowdError(RuntimeError):
@@ -106,6 +115,16 @@ def load_library(path: str = LIB_PATH):
     lib.lowd_last_error.argtypes = [P]
     lib.lowd_launch_count.restype = C.c_uint64
     lib.lowd_launch_count.argtypes = []
+    lib.lowd_batch_create.restype = i32
+    lib.lowd_batch_create.argtypes = [i32, P, P, P, P, i32, P, C.POINTER(P)]
+    lib.lowd_batch_run.restype = i32
+    lib.lowd_batch_run.argtypes = [P, C.POINTER(lowd_batch_options)]
+    lib.lowd_batch_autotune.restype = i32
+    lib.lowd_batch_autotune.argtypes = [P, i32, i32, C.POINTER(lowd_batch_options)]
+    lib.lowd_batch_results.restype = i32
+    lib.lowd_batch_results.argtypes = [P, P, P, P, P, P, P, P]
+    lib.lowd_batch_free.restype = None
+    lib.lowd_batch_free.argtypes = [P]
     lib.lowd_extract_noalloc.restype = i32
     lib.lowd_extract_noalloc.argtypes = [i32, i64, P, P, P, P, P, C.POINTER(i32), C.POINTER(C.c_double), P]
     _lib = lib
@@ -305,3 +324,67 @@ def lowd_free(h: Handle):
     if h is not None and h.ptr and h.ptr.value:
         load_library().lowd_free(h.ptr)
         h.ptr = C.c_void_p(None)
+
+
+class Batch:
+    """A batch of graphs (the C ``lowd_batch``), host mode: numpy in, numpy out."""
+
+    def __init__(self, ptr, B, n_total):
+        self.ptr = C.c_void_p(ptr)
+        self.B = B
+        self.n_total = n_total
+
+    def __del__(self):
+        try:
+            lowd_batch_free(self)
+        except Exception:
+            pass
+
+
+def lowd_batch_create(node_off, edge_off, u, v, stream=None) -> Batch:
+    """Copy a batch: offsets [B+1] (int64) and local-id edges (int32), canonical per graph."""
+    no = np.ascontiguousarray(node_off, dtype=np.int64)
+    eo = np.ascontiguousarray(edge_off, dtype=np.int64)
+    uu = np.ascontiguousarray(u, dtype=np.int32)
+    vv = np.ascontiguousarray(v, dtype=np.int32)
+    B = no.shape[0] - 1
+    out = C.c_void_p()
+    sptr = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    s = load_library().lowd_batch_create(B, no.ctypes.data_as(C.c_void_p), eo.ctypes.data_as(C.c_void_p),
+                                         uu.ctypes.data_as(C.c_void_p), vv.ctypes.data_as(C.c_void_p),
+                                         LOWD_MEM_HOST, sptr, C.byref(out))
+    if s != LOWD_OK:
+        raise LowdError(s, "lowd_batch_create")
+    return Batch(out.value, B, int(no[-1]))
+
+
+def lowd_batch_run(b: Batch, passes: int, ctas_per_sm: int = 0, threads: int = 0, order: int = 0):
+    o = lowd_batch_options(int(passes), int(ctas_per_sm), int(threads), int(order))
+    s = load_library().lowd_batch_run(b.ptr, C.byref(o))
+    if s != LOWD_OK:
+        raise LowdError(s, "lowd_batch_run")
+
+
+def lowd_batch_autotune(b: Batch, passes: int, sample: int = 0) -> dict:
+    o = lowd_batch_options()
+    s = load_library().lowd_batch_autotune(b.ptr, int(passes), int(sample), C.byref(o))
+    if s != LOWD_OK:
+        raise LowdError(s, "lowd_batch_autotune")
+    return {f: getattr(o, f) for f, _ in lowd_batch_options._fields_}
+
+
+def lowd_batch_results(b: Batch) -> dict:
+    rho = np.empty(b.B, np.float64)
+    size, nc, mc, rr, st = (np.empty(b.B, np.int32) for _ in range(5))
+    ins = np.empty(max(b.n_total, 1), np.uint8)
+    P = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    s = load_library().lowd_batch_results(b.ptr, P(rho), P(size), P(ins), P(nc), P(mc), P(rr), P(st))
+    if s != LOWD_OK:
+        raise LowdError(s, "lowd_batch_results")
+    return dict(rho=rho, S_size=size, in_S=ins[:b.n_total], n_core=nc, m_core=mc, rounds=rr, status=st)
+
+
+def lowd_batch_free(b: Batch):
+    if b is not None and b.ptr and b.ptr.value:
+        load_library().lowd_batch_free(b.ptr)
+        b.ptr = C.c_void_p(None)

@@ -16,4 +16,6 @@ from .graphs import (  # noqa: F401
     small_family,
     workload,
     WORKLOADS,
+    batch_graph,
+    batch,
 )

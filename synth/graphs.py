@@ -347,6 +347,28 @@ WORKLOADS = {
 }
 
 
+def batch_graph(g: int, seed_base: int = 1000, n_lo: int = 100, n_hi: int = 20000,
+                d_lo: float = 4.0, d_hi: float = 32.0, gamma_lo: float = 2.1,
+                gamma_hi: float = 2.8, block_frac: float = 0.05, block_p: float = 0.5) -> Graph:
+    """Graph g of the batched workload: a Chung-Lu graph with n ~ U{n_lo..n_hi}, average
+    degree ~ U[d_lo, d_hi], exponent ~ U[gamma_lo, gamma_hi] (drawn from seed
+    seed_base + g), target m = round(n * d / 2), plus a planted block of round(block_frac*n)
+    nodes at pair probability block_p."""
+    rng = np.random.Generator(np.random.PCG64(seed_base + g))
+    n = int(rng.integers(n_lo, n_hi + 1))
+    d = float(rng.uniform(d_lo, d_hi))
+    gamma = float(rng.uniform(gamma_lo, gamma_hi))
+    m = min(int(round(n * d / 2)), n * (n - 1) // 4)
+    bs = max(2, int(round(block_frac * n)))
+    return chung_lu(n, m, gamma, seed=int(rng.integers(0, 2**31 - 1)), block_size=bs, block_p=block_p,
+                    name=f"batch{seed_base}-{g}")
+
+
+def batch(count: int, seed_base: int = 1000, **kw) -> list[Graph]:
+    """The first ``count`` graphs of the batched workload (see :func:`batch_graph`)."""
+    return [batch_graph(g, seed_base=seed_base, **kw) for g in range(count)]
+
+
 def workload(name: str) -> Graph:
     spec = dict(WORKLOADS[name])
     kind = spec.pop("kind")
