@@ -257,6 +257,9 @@ typedef struct {
  *                                   form of Sec. IV: no loops, no repeats)
  * Graphs whose node count exceeds the kernel's shared-memory budget (about 45,000 nodes
  * at one CTA per SM) are reported with status 1 by lowd_batch_results instead of a result.
+ *   stream    cudaStream_t (as void*) for all work of the batch; NULL makes the batch use a
+ *             non-blocking stream of its own (the launch is captured into a CUDA graph, which
+ *             the legacy default stream does not allow)
  */
 lowd_status lowd_batch_create(int32_t B, const int64_t* node_off, const int64_t* edge_off,
                               const int32_t* u, const int32_t* v, int32_t mem, void* stream,

@@ -358,6 +358,7 @@ __global__ void k_batch_check(const int64_t* __restrict__ node_off, const int64_
 
 struct lowd_batch_ctx {
     cudaStream_t st = nullptr;
+    bool own_stream = false;   // created here when the caller passed NULL (capture needs a real stream)
     int mem = LOWD_MEM_HOST;
     int32_t B = 0;
     int64_t n_total = 0, m_total = 0;
@@ -398,6 +399,8 @@ cudaError_t balloc(T** p, size_t count) {
 void batch_free_all(lowd_batch_ctx* b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
+    if (b->own_stream && b->st) cudaStreamDestroy(b->st);
+    b->st = nullptr;
     void* ps[] = {b->node_off, b->edge_off, b->u, b->v, b->eA, b->eB, b->cs, b->oldid, b->order, b->queue,
                   b->rho, b->S_size, b->nH, b->mH, b->rounds, b->status, b->in_S};
     for (void* p : ps)
@@ -483,6 +486,14 @@ lowd_status lowd_batch_create(int32_t B, const int64_t* node_off, const int64_t*
     lowd_batch_ctx* b = new (std::nothrow) lowd_batch_ctx();
     if (!b) return LOWD_ERR_OUT_OF_MEMORY;
     b->st = (cudaStream_t)stream;
+    if (!b->st) {
+        if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return LOWD_ERR_CUDA;
+        }
+        b->own_stream = true;
+    }
     b->mem = mem;
     b->B = B;
     b->h_node_off.resize((size_t)B + 1);
