@@ -281,6 +281,9 @@ lowd_status lowd_batch_autotune(lowd_batch b, int32_t passes, int32_t sample, lo
 lowd_status lowd_batch_results(lowd_batch b, double* rho, int32_t* S_size, uint8_t* in_S,
                                int32_t* n_core, int32_t* m_core, int32_t* rounds, int32_t* status);
 
+/* Text of the last CUDA error seen by this batch ("" if none). */
+const char* lowd_batch_last_error(lowd_batch b);
+
 void lowd_batch_free(lowd_batch b);
 
 /* Release the handle and all its device memory.  NULL is ignored. */

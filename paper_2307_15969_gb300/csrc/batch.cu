@@ -584,7 +584,13 @@ lowd_status lowd_batch_run(lowd_batch b, const lowd_batch_options* opt) {
         set_order(b, o.order, nullptr);
         LaunchCfg cfg;
         e = prepare(o, b->B, &cfg);
-        if (e != cudaSuccess) return b->fail(e);
+        if (e != cudaSuccess) {
+            lowd_status st = b->fail(e);
+            char tmp[200];
+            snprintf(tmp, sizeof(tmp), "prepare: %s", b->err);
+            snprintf(b->err, sizeof(b->err), "%s", tmp);
+            return st;
+        }
         // capture the launch (queue reset + persistent kernel) once, replay it afterwards
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
@@ -595,7 +601,13 @@ lowd_status lowd_batch_run(lowd_batch b, const lowd_batch_options* opt) {
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return b->fail(e);
+        if (e != cudaSuccess) {
+            lowd_status st = b->fail(e);
+            char tmp[200];
+            snprintf(tmp, sizeof(tmp), "capture: %s", b->err);
+            snprintf(b->err, sizeof(b->err), "%s", tmp);
+            return st;
+        }
         b->gopt = o;
     }
     e = cudaGraphLaunch(b->gexec, b->st);
@@ -666,6 +678,8 @@ lowd_status lowd_batch_results(lowd_batch b, double* rho, int32_t* S_size, uint8
     if (e != cudaSuccess) return b->fail(e);
     return LOWD_OK;
 }
+
+const char* lowd_batch_last_error(lowd_batch b) { return b ? b->err : ""; }
 
 void lowd_batch_free(lowd_batch b) {
     if (!b) return;

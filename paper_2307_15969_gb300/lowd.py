@@ -35,7 +35,7 @@ EXPORTED = (
     "lowd_get_prune_info", "lowd_get_edge_order", "lowd_free", "lowd_status_string",
     "lowd_last_error", "lowd_launch_count", "lowd_extract_noalloc",
     "lowd_batch_create", "lowd_batch_run", "lowd_batch_autotune", "lowd_batch_results",
-    "lowd_batch_free",
+    "lowd_batch_free", "lowd_batch_last_error",
 )
 LOWD_BATCH_ORDER_AS_GIVEN = 1
 LOWD_BATCH_ORDER_LARGEST_FIRST = 2
@@ -123,6 +123,8 @@ def load_library(path: str = LIB_PATH):
     lib.lowd_batch_autotune.argtypes = [P, i32, i32, C.POINTER(lowd_batch_options)]
     lib.lowd_batch_results.restype = i32
     lib.lowd_batch_results.argtypes = [P, P, P, P, P, P, P, P]
+    lib.lowd_batch_last_error.restype = C.c_char_p
+    lib.lowd_batch_last_error.argtypes = [P]
     lib.lowd_batch_free.restype = None
     lib.lowd_batch_free.argtypes = [P]
     lib.lowd_extract_noalloc.restype = i32
@@ -362,14 +364,14 @@ def lowd_batch_run(b: Batch, passes: int, ctas_per_sm: int = 0, threads: int = 0
     o = lowd_batch_options(int(passes), int(ctas_per_sm), int(threads), int(order))
     s = load_library().lowd_batch_run(b.ptr, C.byref(o))
     if s != LOWD_OK:
-        raise LowdError(s, "lowd_batch_run")
+        raise LowdError(s, "lowd_batch_run", load_library().lowd_batch_last_error(b.ptr).decode())
 
 
 def lowd_batch_autotune(b: Batch, passes: int, sample: int = 0) -> dict:
     o = lowd_batch_options()
     s = load_library().lowd_batch_autotune(b.ptr, int(passes), int(sample), C.byref(o))
     if s != LOWD_OK:
-        raise LowdError(s, "lowd_batch_autotune")
+        raise LowdError(s, "lowd_batch_autotune", load_library().lowd_batch_last_error(b.ptr).decode())
     return {f: getattr(o, f) for f, _ in lowd_batch_options._fields_}
 
 
