@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int32_t red[32];
     __shared__ int32_t s_graph, s_count, s_rem;
+    __shared__ volatile int32_t s_bad;   // an edge id outside the core: recorded, never used
     const int tid = threadIdx.x;
     const int nt = blockDim.x;
     for (;;) {
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
         }
         __syncthreads();
         const int32_t g = s_graph;
+        if (tid == 0) s_bad = 0;
         __syncthreads();
         if (g < 0) break;
         const int64_t n0 = A.node_off[g], m0 = A.edge_off[g];
@@ -226,12 +228,14 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
             nxt[pos] = p;
             cs[pos] = 0.5f;          // Algorithm 1: f_e(u) = f_e(v) = w_e / 2
         }
+        __syncthreads();             // the counters below reuse `cursor`
         // initial loads: degree in the core / 2
         int32_t* dH = cursor;  // reuse (P + 1 >= nH)
         for (int32_t i = tid; i < nH; i += nt) dH[i] = 0;
         __syncthreads();
         for (int32_t e = tid; e < mH; e += nt) {
             const uint32_t p = nxt[e];
+            if ((int32_t)(p & 0xffffu) >= nH || (int32_t)(p >> 16) >= nH) { s_bad = 1; continue; }
             atomicAdd(&dH[p & 0xffffu], 1);
             atomicAdd(&dH[p >> 16], 1);
         }
@@ -245,6 +249,7 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
                 for (int32_t i = beg + tid; i < end; i += nt) {
                     const uint32_t p = __ldcg(nxt + i);
                     const int32_t a = (int32_t)(p & 0xffffu), b = (int32_t)(p >> 16);
+                    if (a >= nH || b >= nH) { s_bad = 1; continue; }   // never taken: ids checked
                     float la = L[a], lb = L[b], s = __ldcg(cs + i);
                     const float diff = la - lb;
                     const bool gt = diff > 0.0f;
@@ -292,6 +297,7 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
         __syncthreads();
         for (int32_t e = tid; e < mH; e += nt) {
             const uint32_t p = nxt[e];
+            if ((int32_t)(p & 0xffffu) >= nH || (int32_t)(p >> 16) >= nH) { s_bad = 1; continue; }
             atomicAdd(&bucket[max(pos[p & 0xffffu], pos[p >> 16])], 1);
         }
         __syncthreads();
@@ -322,7 +328,7 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
             s_rem = (int32_t)k2;
             A.rho[g] = k2 > 0 ? (double)W2 / (double)k2 : 0.0;
             A.S_size[g] = (int32_t)k2;
-            A.nH[g] = nH; A.mH[g] = mH; A.rounds[g] = r; A.status[g] = BS_OK;
+            A.nH[g] = nH; A.mH[g] = mH; A.rounds[g] = r; A.status[g] = s_bad ? BS_BAD_INPUT : BS_OK;
         }
         __syncthreads();
         const int32_t kstar = s_rem;
