@@ -617,6 +617,7 @@ lowd_status lowd_batch_run(lowd_batch b, const lowd_batch_options* opt) {
         b->gopt = o;
     }
     e = cudaGraphLaunch(b->gexec, b->st);
+    lowd_note_launch();   // the replayed graph holds one kernel
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return b->fail(e);
     return LOWD_OK;

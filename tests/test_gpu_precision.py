@@ -1,0 +1,75 @@
+"""Precision of the FP32 sweep against the FP64 oracle on the weighted R-MAT recipe
+(scale 16, edge factor 8, lognormal(0,1) weights on the 2^-20 grid, 128-node block with
+weights x3).
+
+The oracle replays the GPU's exact edge order in FP64; the test bounds and prints the
+relative load error max|l_gpu - l_64| / max l_64, the relative error of sum(l^2), and the
+density gap, after 1, 10, 100 and 400 passes.  Pruning and the pruned graph are bit-exact;
+the extraction on the GPU's loads is bit-exact.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+LOAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def setup():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_15969_gb300 import build
+    build.build()
+    import paper_2307_15969_gb300 as pkg
+    import oracle
+    oracle.build()
+    return torch, pkg, oracle, synth.workload("rmat16w")
+
+
+def test_weighted_rmat_precision_against_fp64(setup, capsys):
+    torch, pkg, orc, g = setup
+    h = pkg.lowd_load_graph(g.n, torch.from_numpy(g.u).cuda(), torch.from_numpy(g.v).cuda(),
+                            torch.from_numpy(g.w).cuda())
+    nk, mk, rounds = pkg.lowd_prune(h)
+    wu, scale = orc.weight_units(g.m, g.w)
+    pr = orc.prune(g.n, g.u, g.v, wu, True)
+    assert np.array_equal(pkg.lowd_get_prune_info(h)[1].cpu().numpy(), pr["removal_round"])
+    keep = pr["removal_round"] < 0
+    nh, uh, vh, wh, idmap = orc.compact(g.n, g.u, g.v, g.w, keep)
+    gu, gv, gw = (x.cpu().numpy() for x in pkg.lowd_get_graph(h))
+    assert np.array_equal(gu, uh) and np.array_equal(gv, vh) and np.array_equal(gw, wh)
+    pkg.lowd_iterate(h, 1)
+    order = pkg.lowd_get_edge_order(h)[0].cpu().numpy()
+    o = orc.LowdState(nh, uh, vh, wh.astype(np.float64))
+    o.iterate(1, order=order)
+    done = 1
+    report = []
+    whu, _ = orc.weight_units(uh.shape[0], wh)
+    for T in (1, 10, 100, 400):
+        if T > done:
+            st = pkg.lowd_iterate(h, T - done)
+            o.iterate(T - done, order=order)
+            done = T
+        else:
+            st = pkg.lowd_iterate(h, 0)
+        lg = pkg.lowd_get_loads(h).cpu().numpy().astype(np.float64)
+        s64 = o.stats()
+        lerr = np.max(np.abs(lg - o.l)) / o.l.max()
+        qerr = abs(st["sum_load_sq"] - s64[1]) / s64[1]
+        S, rho, _ = pkg.lowd_extract(h, want_loads=False)
+        So, Wo = orc.extract(nh, uh, vh, whu, lg)
+        assert np.array_equal(S.cpu().numpy(), idmap[So])
+        assert rho == Wo / scale / So.shape[0]
+        report.append((T, lerr, qerr, rho, st["max_load"]))
+        assert lerr <= LOAD_TOL, (T, lerr)
+        assert qerr <= 1e-5, (T, qerr)
+    with capsys.disabled():
+        print(f"\n[precision] weighted rmat16w core n={nh} m={uh.shape[0]} (prune rounds {rounds})")
+        for T, lerr, qerr, rho, D in report:
+            print(f"[precision] passes={T:4d} load err {lerr:.2e}  sum-sq err {qerr:.2e}  "
+                  f"rho(S)={rho:.6f}  D={D:.6f}  gap={(D - rho) / rho:.2e}")
+    pkg.lowd_free(h)
