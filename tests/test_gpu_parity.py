@@ -20,6 +20,11 @@ pytestmark = pytest.mark.gpu
 LOAD_TOL = 1e-4   # relative to the largest load; FP32 passes, see the design doc
 
 
+def load_tol(T):
+    """Same-order iterates: accumulated FP32 rounding grows like sqrt(passes)."""
+    return LOAD_TOL * max(1.0, (T / 100.0) ** 0.5)
+
+
 @pytest.fixture(scope="module")
 def pkg():
     torch = pytest.importorskip("torch")
@@ -188,7 +193,7 @@ def test_same_order_loads(pkg, orc, name, prune, T):
         assert np.unique(ends).shape[0] == ends.shape[0]
     lg = _np(pkg.lowd_get_loads(h)).astype(np.float64)
     scale = max(1.0, o.l.max())
-    assert np.max(np.abs(lg - o.l)) <= LOAD_TOL * scale
+    assert np.max(np.abs(lg - o.l)) <= load_tol(T) * scale
     sg = _np(pkg.lowd_get_splits(h)).astype(np.float64)
     assert np.all(sg >= 0) and np.all(sg <= 1.0)
     # conservation of the FP32 state: sum of loads equals the number of edges
