@@ -73,7 +73,9 @@ typedef struct {
                              best prefix of the load order (default 0: run all k passes) */
     int32_t schedule;     /* 0 = automatic; 1 = one-CTA shared-memory sweep (node count
                              must fit shared memory); 2 = grid sweep over matchings */
-    int32_t reserved;
+    int32_t rederive_every; /* re-derive the FP32 loads from the splits (FP64 sums) after at
+                             most this many passes, bounding the drift of the running FP32
+                             loads: 0 = default 50, < 0 = only at the end of the call */
 } lowd_options;
 
 /* Statistics of the state after lowd_iterate (FP64, from loads re-derived from the

@@ -888,9 +888,13 @@ lowd_status lowd_sweep_run(lowd_ctx* h, int32_t k, const lowd_options* opt, lowd
     int converged = 0;
     double rho_best = 0.0;
     int32_t best_size = 0;
+    const int32_t R = o.rederive_every == 0 ? 50 : (o.rederive_every < 0 ? 0x7fffffff : o.rederive_every);
+    int32_t since = 0;        // passes since the loads were last re-derived from the splits
+    int32_t since_check = 0;  // passes since the last check
     while (done < k) {
         int32_t step = k - done;
-        if (o.check_every > 0 && o.check_every < step) step = o.check_every;
+        if (o.check_every > 0 && o.check_every - since_check < step) step = o.check_every - since_check;
+        if (R - since < step) step = R - since;
         LOWD_CK(run_passes(h, step));
         LOWD_CK(cudaMemcpyAsync(h->h_pin + 8, h->d_i32 + 8, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
         LOWD_CK(cudaStreamSynchronize(h->st));
@@ -900,8 +904,17 @@ lowd_status lowd_sweep_run(lowd_ctx* h, int32_t k, const lowd_options* opt, lowd
         }
         done += step;
         h->iters += step;
-        if (o.check_every > 0) {
+        since += step;
+        since_check += step;
+        const bool check = o.check_every > 0 && (since_check >= o.check_every || done == k);
+        if (since >= R && !check && done < k) {
             LOWD_TRY(lowd_sweep_rederive(h, st3));
+            since = 0;
+        }
+        if (check) {
+            LOWD_TRY(lowd_sweep_rederive(h, st3));
+            since = 0;
+            since_check = 0;
             int64_t Wb = 0;
             int32_t kb = 0;
             LOWD_TRY(lowd_extract_best(h, h->l, nullptr, &kb, &Wb));
