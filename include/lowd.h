@@ -174,6 +174,25 @@ lowd_status lowd_extract(lowd_handle h, int32_t* S, int32_t* S_size, double* rho
 
 /* ------------------------------------------------------------------ state and parity hooks */
 
+/*
+ * lowd_get_ldd - the locally-dense decomposition read off the current loads (Sec. II,
+ * Definition of LDD; Properties 1-2: the nodes of B_i \ B_{i-1} all carry load lambda_i,
+ * lambda_1 > lambda_2 > ...).  Nodes of the current graph are ordered by load descending
+ * (ties by id descending); a shell ends where the next load is lower by more than
+ * rel_tol times the current one.  lambda_i = (W(B_i) - W(B_{i-1})) / |B_i \ B_{i-1}| is
+ * computed exactly from integer prefix weights, so on converged loads it is the exact shell
+ * density whenever the shells are separated by more than the loads' error.  B_1 with
+ * lambda_1 is the maximal densest subgraph; Corollary 1's bounds for the densest
+ * k-subgraph follow from (shell_end, lambda).
+ *   shell      out [n_orig]: 1-based shell of each original node; 0 for pruned nodes
+ *   lambda     out [capacity n]: lambda_i per shell
+ *   shell_end  out [capacity n]: |B_i| (shell i covers sorted positions shell_end[i-1]..)
+ *   n_shells   host out: number of shells
+ * Any of shell / lambda / shell_end may be NULL.
+ */
+lowd_status lowd_get_ldd(lowd_handle h, double rel_tol, int32_t* shell, double* lambda,
+                         int32_t* shell_end, int32_t* n_shells);
+
 /* Current graph sizes and schedule.  info: host pointer. */
 lowd_status lowd_get_info(lowd_handle h, lowd_info* info);
 

@@ -239,6 +239,32 @@ lowd_status lowd_extract(lowd_handle h, int32_t* S, int32_t* S_size, double* rho
     return s;
 }
 
+lowd_status lowd_get_ldd(lowd_handle h, double rel_tol, int32_t* shell, double* lambda, int32_t* shell_end,
+                         int32_t* n_shells) {
+    LOWD_TRY(check_handle(h));
+    if (!n_shells || !(rel_tol >= 0.0)) return LOWD_ERR_INVALID_ARG;
+    float* l = nullptr;
+    int32_t *sh = nullptr, *se = nullptr;
+    double* lam = nullptr;
+    lowd_status s = LOWD_OK;
+    do {
+        if ((s = current_loads(h, &l))) break;
+        if ((s = dalloc(h, &sh, h->n0))) break;
+        if ((s = dalloc(h, &se, h->n))) break;
+        if ((s = dalloc(h, &lam, h->n))) break;
+        int32_t ns = 0;
+        if ((s = lowd_ldd_export(h, l, rel_tol, sh, se, lam, &ns))) break;
+        if ((s = to_caller(h, shell, sh, (size_t)h->n0))) break;
+        if ((s = to_caller(h, shell_end, se, (size_t)ns))) break;
+        if ((s = to_caller(h, lambda, lam, (size_t)ns))) break;
+        cudaError_t e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) { s = h->fail(e); break; }
+        *n_shells = ns;
+    } while (0);
+    dfree(&l); dfree(&sh); dfree(&se); dfree(&lam);
+    return s;
+}
+
 lowd_status lowd_get_info(lowd_handle h, lowd_info* info) {
     LOWD_TRY(check_handle(h));
     if (!info) return LOWD_ERR_INVALID_ARG;

@@ -135,3 +135,5 @@ lowd_status lowd_sweep_edge_order(lowd_ctx* h, int32_t* out_dev);
 // extract.cu
 lowd_status lowd_extract_best(lowd_ctx* h, const float* loads_dev, int32_t* S_dev_current,
                               int32_t* S_size, int64_t* W_best);
+lowd_status lowd_ldd_export(lowd_ctx* h, const float* loads_dev, double rel_tol, int32_t* shell_orig,
+                            int32_t* shell_end, double* lam, int32_t* ns_out);

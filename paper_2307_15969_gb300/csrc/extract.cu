@@ -322,3 +322,111 @@ extern "C" lowd_status lowd_extract_noalloc(int32_t n, int64_t m, const int32_t*
     *rho = best.k > 0 ? (double)best.W / scale / (double)best.k : 0.0;
     return LOWD_OK;
 }
+
+// ------------------------------------------------------------------ LDD export
+//
+// The locally-dense decomposition read off converged loads (Sec. II, Definition of LDD;
+// Properties 1-2: every node of B_i \ B_{i-1} carries the load lambda_i and
+// lambda_1 > lambda_2 > ...).  Nodes in descending (load, id) order; a shell ends where the
+// next load is lower by more than rel_tol of the current one; lambda_i is then computed
+// exactly from the integer prefix weights: (W(B_i) - W(B_{i-1})) / |B_i \ B_{i-1}|.
+
+namespace {
+
+__global__ void k_ldd_cuts(const float* __restrict__ l, const int32_t* __restrict__ order, int32_t n,
+                           double rel_tol, int32_t* __restrict__ cut) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i == n - 1) { cut[i] = 1; continue; }
+        const double a = (double)l[order[i]], b = (double)l[order[i + 1]];
+        cut[i] = (a - b) > rel_tol * fabs(a) ? 1 : 0;
+    }
+}
+
+// shell of sorted position i = cuts before i; position i closing shell j records its end
+__global__ void k_ldd_emit(const int32_t* __restrict__ order, const int32_t* __restrict__ cut,
+                           const int32_t* __restrict__ cpos, int32_t n, const int32_t* __restrict__ map,
+                           int32_t* __restrict__ shell_orig, int32_t* __restrict__ shell_end) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = order[i];
+        shell_orig[map ? map[x] : x] = cpos[i] + 1;   // 1-based shell index
+        if (cut[i]) shell_end[cpos[i]] = (int32_t)i + 1;
+    }
+}
+
+// lambda_j from the prefix weights W(S_k) = excl[k] (k < n), W(S_n) = excl[n-1] + bucket[n-1]
+__global__ void k_ldd_lambda(const int32_t* __restrict__ shell_end, int32_t ns, const int64_t* __restrict__ excl,
+                             const unsigned long long* __restrict__ bucket, int32_t n, double scale,
+                             double* __restrict__ lam) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ns;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = shell_end[j];
+        const int32_t b = j > 0 ? shell_end[j - 1] : 0;
+        const int64_t We = e < n ? excl[e] : excl[n - 1] + (int64_t)bucket[n - 1];
+        const int64_t Wb = b == 0 ? 0 : (b < n ? excl[b] : excl[n - 1] + (int64_t)bucket[n - 1]);
+        lam[j] = (double)(We - Wb) / scale / (double)(e - b);
+    }
+}
+
+__global__ void k_fill_i32_x(int32_t* __restrict__ x, int64_t n, int32_t val) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = val;
+}
+
+}  // namespace
+
+// shell_orig [n0] (device), shell_end [n] (device), lam [n] (device); *ns host
+lowd_status lowd_ldd_export(lowd_ctx* h, const float* loads_dev, double rel_tol, int32_t* shell_orig,
+                            int32_t* shell_end, double* lam, int32_t* ns_out) {
+    cudaStream_t st = h->st;
+    const int32_t n = h->n;
+    const int64_t m = h->m;
+    uint32_t* key[2] = {nullptr, nullptr};
+    int32_t* val[2] = {nullptr, nullptr};
+    int32_t *pos = nullptr, *cut = nullptr, *cpos = nullptr;
+    unsigned long long* bucket = nullptr;
+    int64_t* excl = nullptr;
+    lowd_status s = LOWD_OK;
+    auto cleanup = [&]() {
+        dfree(&key[0]); dfree(&key[1]); dfree(&val[0]); dfree(&val[1]); dfree(&pos);
+        dfree(&cut); dfree(&cpos); dfree(&bucket); dfree(&excl);
+    };
+    do {
+        if ((s = h->need_tmp(lowd_sort_tmp_bytes(m > n ? m : n)))) break;
+        if ((s = dalloc(h, &key[0], n))) break;
+        if ((s = dalloc(h, &key[1], n))) break;
+        if ((s = dalloc(h, &val[0], n))) break;
+        if ((s = dalloc(h, &val[1], n))) break;
+        if ((s = dalloc(h, &pos, n))) break;
+        if ((s = dalloc(h, &cut, n))) break;
+        if ((s = dalloc(h, &cpos, n))) break;
+        if ((s = dalloc(h, &bucket, n))) break;
+        if ((s = dalloc(h, &excl, n))) break;
+        LOWD_LAUNCH(k_load_keys, grid_for(n), kT, 0, st, loads_dev, n, key[0], val[0]);
+        const int cur = radix_sort_pairs<uint32_t, int32_t>(key[0], val[0], key[1], val[1], n, 32, h->tmp, st);
+        int32_t* order = val[cur];
+        LOWD_LAUNCH(k_positions, grid_for(n), kT, 0, st, order, n, pos);
+        cudaMemsetAsync(bucket, 0, sizeof(unsigned long long) * (size_t)n, st);
+        if (m > 0) LOWD_LAUNCH(k_edge_buckets, grid_for(m), kT, 0, st, h->u, h->v, h->wu, m, pos, bucket);
+        scan_exclusive<int64_t>((const int64_t*)bucket, excl, n, nullptr, h->tmp, st);
+        LOWD_LAUNCH(k_ldd_cuts, grid_for(n), kT, 0, st, loads_dev, order, n, rel_tol, cut);
+        scan_exclusive<int32_t>(cut, cpos, n, h->d_i32 + 9, h->tmp, st);
+        LOWD_LAUNCH(k_fill_i32_x, grid_for(h->n0), kT, 0, st, shell_orig, (int64_t)h->n0, 0);
+        LOWD_LAUNCH(k_ldd_emit, grid_for(n), kT, 0, st, order, cut, cpos, n, h->map, shell_orig, shell_end);
+        int32_t ns = 0;
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&ns, h->d_i32 + 9, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { s = h->fail(e); break; }
+        const double scale = h->wu ? 1048576.0 : 1.0;
+        LOWD_LAUNCH(k_ldd_lambda, grid_for(ns), kT, 0, st, shell_end, ns, excl, bucket, n, scale, lam);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { s = h->fail(e); break; }
+        *ns_out = ns;
+    } while (0);
+    cleanup();
+    return s;
+}

@@ -35,7 +35,7 @@ EXPORTED = (
     "lowd_get_prune_info", "lowd_get_edge_order", "lowd_free", "lowd_status_string",
     "lowd_last_error", "lowd_launch_count", "lowd_extract_noalloc",
     "lowd_batch_create", "lowd_batch_run", "lowd_batch_autotune", "lowd_batch_results",
-    "lowd_batch_free", "lowd_batch_last_error",
+    "lowd_batch_free", "lowd_batch_last_error", "lowd_get_ldd",
 )
 LOWD_BATCH_ORDER_AS_GIVEN = 1
 LOWD_BATCH_ORDER_LARGEST_FIRST = 2
@@ -93,6 +93,8 @@ def load_library(path: str = LIB_PATH):
     lib.lowd_iterate.argtypes = [P, i32, C.POINTER(lowd_options), C.POINTER(lowd_stats)]
     lib.lowd_extract.restype = i32
     lib.lowd_extract.argtypes = [P, P, C.POINTER(i32), C.POINTER(C.c_double), P]
+    lib.lowd_get_ldd.restype = i32
+    lib.lowd_get_ldd.argtypes = [P, C.c_double, P, P, P, C.POINTER(i32)]
     lib.lowd_get_info.restype = i32
     lib.lowd_get_info.argtypes = [P, C.POINTER(lowd_info)]
     lib.lowd_get_graph.restype = i32
@@ -253,6 +255,25 @@ def lowd_extract(h: Handle, want_loads: bool = True):
     h._check(load_library().lowd_extract(h.ptr, h.ptr_of(S), C.byref(k), C.byref(rho),
                                          h.ptr_of(loads)), "lowd_extract")
     return S[:k.value], rho.value, (loads[:h.n0] if loads is not None else None)
+
+
+def lowd_get_ldd(h: Handle, rel_tol: float = 1e-5):
+    """Locally-dense decomposition of the current loads: (shell per original node, 0 =
+    pruned; lambda per shell; |B_i| per shell)."""
+    n = lowd_get_info(h)["n"]
+    shell = h.empty(h.n0, np.int32)
+    if h.device:
+        import torch
+        lam = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+        lamp = C.c_void_p(lam.data_ptr())
+    else:
+        lam = np.empty(max(n, 1), np.float64)
+        lamp = lam.ctypes.data_as(C.c_void_p)
+    end = h.empty(n, np.int32)
+    ns = C.c_int32()
+    h._check(load_library().lowd_get_ldd(h.ptr, float(rel_tol), h.ptr_of(shell), lamp, h.ptr_of(end),
+                                         C.byref(ns)), "lowd_get_ldd")
+    return shell[:h.n0], lam[:ns.value], end[:ns.value]
 
 
 def lowd_get_info(h: Handle) -> dict:
