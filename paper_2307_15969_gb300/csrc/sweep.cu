@@ -22,6 +22,7 @@
 // f_e(hi) = w_e - s_e (the tighter dual's equality f_e(u) + f_e(v) = w_e, Sec. III-B).
 #include "ctx.cuh"
 #include "prims.cuh"
+#include "async.cuh"
 
 using namespace lowd;
 
@@ -355,76 +356,6 @@ k_sweep_vec(int32_t n, int32_t C, const int32_t* __restrict__ coff,
 // Every wait on an mbarrier is bounded; on expiry the kernel records an error flag and
 // all threads leave the loop together.
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// try_wait that lets the hardware suspend the thread for up to hint_ns before returning
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void bulk_wait_read() {
-    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
-}
-
-template <int N>
-__device__ __forceinline__ void bulk_wait() {
-    asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
 constexpr int kTmaConsumers = 992;   // one edge per consumer thread per class
 constexpr int kTmaMaxStages = 16;
 constexpr int kStoreSlack = 1;    // bulk stores allowed to be still reading their stage
@@ -446,28 +377,6 @@ __host__ __device__ inline TmaLayout tma_layout(int32_t n, int32_t C, int32_t S,
     t.stage_bytes = t.arr_bytes * (weighted ? 3u : 2u);
     t.total = t.stages + t.stage_bytes * (uint32_t)S;
     return t;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void consumer_sync(int nc) {  // bar.sync over the consumer warps
-    asm volatile("bar.sync 1, %0;" ::"r"(nc) : "memory");
-}
-
-// bar.sync over the consumer warps that also ORs a predicate across them
-__device__ __forceinline__ bool consumer_sync_or(int nc, bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, 1, %2, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)pred), "r"(nc)
-        : "memory");
-    return r != 0;
 }
 
 template <bool WEIGHTED, int E>
@@ -520,7 +429,8 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
             while (pf < ahead && pf < P) fill();
             int32_t k = 0, j = 0;
             uint32_t parity = 0;
-            for (int32_t q = 0; q < P; ++q) {
+            int32_t q = 0;
+            for (; q < P; ++q) {
                 uint32_t spins = 0;
                 bool ok = mbar_try_wait_sleep(&empty[k], parity, 1000);
                 while (!ok && !abort_flag && ++spins < kWaitLimit) ok = mbar_try_wait_sleep(&empty[k], parity, 1000);
@@ -538,6 +448,8 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
                 if (++k == S) { k = 0; parity ^= 1u; }
                 j = (j + 1 == NC) ? 0 : j + 1;
             }
+            // fills [q, pf) were never handed back: on abort wait (bounded) for them to land
+            if (q < P) drain_fills(full, S, q, pf, kWaitLimit);
             bulk_wait<0>();
             if (abort_flag) atomicOr(err, 1);
         }
