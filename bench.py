@@ -211,7 +211,7 @@ def run_batch(args):
     pkg.load_library()
     T = args.iters
     b = pkg.lowd_batch_create(node_off, edge_off, u, v)
-    tuned = pkg.lowd_batch_autotune(b, passes=T, sample=min(count, 512))
+    tuned = pkg.lowd_batch_autotune(b, passes=T, sample=0)   # every graph: a sample mis-ranks schedules
     for _ in range(args.warmup):
         pkg.lowd_batch_run(b, passes=T)
     times = []

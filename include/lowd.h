@@ -264,7 +264,7 @@ enum { LOWD_BATCH_ORDER_AS_GIVEN = 1, LOWD_BATCH_ORDER_LARGEST_FIRST = 2 };
 /* Launch schedule of lowd_batch_run; zero fields take the autotuned (or default) value. */
 typedef struct {
     int32_t passes;       /* LOWD passes per graph (>= 0) */
-    int32_t ctas_per_sm;  /* 1 or 2 (shared memory is split between them) */
+    int32_t ctas_per_sm;  /* 1 to 4 (shared memory is split between them) */
     int32_t threads;      /* threads per CTA: multiple of 32 in [64, 1024] */
     int32_t order;        /* LOWD_BATCH_ORDER_* : order in which graphs enter the queue */
 } lowd_batch_options;
@@ -298,9 +298,17 @@ lowd_status lowd_batch_autotune(lowd_batch b, int32_t passes, int32_t sample, lo
 /* Per-graph results of the last run, all arrays optional, host or device per `mem`:
  * rho [B] (W(S*)/|S*|), S_size [B], in_S [node_off[B]] (1 if the node is in S*, by local
  * id), n_core / m_core [B] (size of the pruned graph), rounds [B] (pruning rounds),
- * status [B] (0 ok, 1 too many nodes, 2 pruned core too large for the extraction). */
+ * status [B] (0 ok, 1 too many nodes, 2 pruned core too large for the extraction, 3 an
+ * internal edge-id check failed, 4 a bounded wait of the staged passes expired; 3 and 4
+ * mark a defect, the graph's result is not valid). */
 lowd_status lowd_batch_results(lowd_batch b, double* rho, int32_t* S_size, uint8_t* in_S,
                                int32_t* n_core, int32_t* m_core, int32_t* rounds, int32_t* status);
+
+/* FP32 load of every node after the last run's passes, by local id, host or device per
+ * `mem`: loads [node_off[B]]; 0 for nodes removed by Algorithm 2 and for graphs with a
+ * nonzero status.  Inside each graph the passes visit the core's colour classes (the
+ * circle colouring of the core, ids renumbered ascending) in ascending colour. */
+lowd_status lowd_batch_loads(lowd_batch b, float* loads);
 
 /* Text of the last CUDA error seen by this batch ("" if none). */
 const char* lowd_batch_last_error(lowd_batch b);

@@ -206,6 +206,32 @@ class LowdState:
         return float(out[0]), float(out[1]), float(out[2])
 
 
+def circle_order(n, u, v):
+    """The pass order of the parallel schedule, computed here from its definition.
+
+    Algorithm 1 visits the edges one after another in any fixed order.  The GPU path
+    groups them into the colour classes of the round-robin ("circle") tournament
+    colouring of the complete graph on n nodes: with N' = n rounded up to even and
+    P = N' - 1 (P = 1 when that is 0), edge {a, b}, a < b, has colour (a + b) mod P, or
+    2a mod P when b = N' - 1.  Each class is a matching, so the order inside a class
+    does not change the result of a pass; classes are visited in ascending colour.
+    Returns (order, class_offsets[P + 1], colour): order lists edge ids class by class
+    (by edge id inside a class).
+
+    Parity pinned by tests/test_oracle_schedule.py: on K_n every class is a perfect (n
+    even) or near-perfect (n odd) matching and every pair has exactly one colour; on
+    random graphs every class is a matching."""
+    u = np.asarray(u, np.int64)
+    v = np.asarray(v, np.int64)
+    a, b = np.minimum(u, v), np.maximum(u, v)
+    Np = int(n) + (int(n) & 1)
+    P = max(Np - 1, 1)
+    colour = np.where(b == Np - 1, (2 * a) % P, (a + b) % P)
+    order = np.argsort(colour, kind="stable").astype(np.int32)
+    offs = np.searchsorted(colour[order], np.arange(P + 1)).astype(np.int64)
+    return order, offs, colour
+
+
 def extract(n, u, v, wu, loads):
     """Algorithm 1's extraction.  Returns (S* ids ascending, W(S*) in units)."""
     lib = _load()

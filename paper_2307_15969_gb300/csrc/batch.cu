@@ -17,6 +17,7 @@
 // beyond report a status instead of a result.
 #include "ctx.cuh"
 #include "prims.cuh"
+#include "async.cuh"
 
 #include <vector>
 #include <algorithm>
@@ -26,8 +27,13 @@ using namespace lowd;
 namespace {
 
 constexpr int kBT = 512;  // threads per CTA (default)
+// staged passes (producer warp + bulk copies), as in the single-graph sweep
+constexpr int kBMaxStages = 8;
+constexpr int kBStoreSlack = 1;
+constexpr int kBStoreGroups = 8;
+constexpr uint32_t kBWaitLimit = 1u << 22;
 
-enum { BS_OK = 0, BS_TOO_MANY_NODES = 1, BS_CORE_TOO_LARGE = 2, BS_BAD_INPUT = 3 };
+enum { BS_OK = 0, BS_TOO_MANY_NODES = 1, BS_CORE_TOO_LARGE = 2, BS_BAD_INPUT = 3, BS_WAIT_EXPIRED = 4 };
 
 struct BatchArgs {
     int32_t B;
@@ -35,9 +41,9 @@ struct BatchArgs {
     const int64_t* edge_off;   // [B+1]
     const int32_t* u;          // [m_total] local ids, u < v, strictly increasing per graph
     const int32_t* v;
-    uint32_t* eA;              // [m_total] scratch: packed edges (ping)
-    uint32_t* eB;              // [m_total] scratch: packed edges (pong / class-major)
-    float* cs;                 // [m_total] scratch: splits in class-major order
+    uint32_t* eA;              // [m_total + 4 n_total + 16] scratch: packed edges (ping)
+    uint32_t* eB;              // same size: packed edges (pong / class-major, padded)
+    float* cs;                 // same size: splits in class-major order
     int32_t* oldid;            // [n_total] scratch: core id -> local id
     const int32_t* order;      // [B] processing order
     int32_t* queue;            // work counter
@@ -50,6 +56,7 @@ struct BatchArgs {
     int32_t* rounds;           // [B]
     int32_t* status;           // [B]
     uint8_t* in_S;             // [n_total]
+    float* loads;              // [n_total] loads after the passes (0 for pruned nodes)
 };
 
 __device__ __forceinline__ int32_t block_sum_i32(int32_t x, int32_t* red) {
@@ -92,6 +99,8 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
     __shared__ int32_t red[32];
     __shared__ int32_t s_graph, s_count, s_rem;
     __shared__ volatile int32_t s_bad;   // an edge id outside the core: recorded, never used
+    __shared__ volatile int32_t s_abort; // a bounded wait of the staged passes expired
+    __shared__ int32_t s_stage_len;
     const int tid = threadIdx.x;
     const int nt = blockDim.x;
     for (;;) {
@@ -101,7 +110,7 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
         }
         __syncthreads();
         const int32_t g = s_graph;
-        if (tid == 0) s_bad = 0;
+        if (tid == 0) { s_bad = 0; s_abort = 0; }
         __syncthreads();
         if (g < 0) break;
         const int64_t n0 = A.node_off[g], m0 = A.edge_off[g];
@@ -109,12 +118,16 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
         const int32_t m = (int32_t)(A.edge_off[g + 1] - m0);
         const int32_t* gu = A.u + m0;
         const int32_t* gv = A.v + m0;
-        uint32_t* eA = A.eA + m0;
-        uint32_t* eB = A.eB + m0;
-        float* cs = A.cs + m0;
+        // scratch range of this graph: m edges plus up to 3 padding slots per class (<= n
+        // classes), starting on a 16-byte boundary
+        const int64_t so = ((m0 + 4 * n0) + 3) & ~(int64_t)3;
+        uint32_t* eA = A.eA + so;
+        uint32_t* eB = A.eB + so;
+        float* cs = A.cs + so;
         int32_t* oldid = A.oldid + n0;
         uint8_t* inS = A.in_S + n0;
-        for (int32_t i = tid; i < n; i += nt) inS[i] = 0;
+        float* lout = A.loads + n0;
+        for (int32_t i = tid; i < n; i += nt) { inS[i] = 0; lout[i] = 0.0f; }
         if ((uint64_t)n * 5u + 64u > A.smem_bytes || n > 65535) {
             if (tid == 0) { A.status[g] = BS_TOO_MANY_NODES; A.rho[g] = 0.0; A.S_size[g] = 0; }
             continue;
@@ -206,11 +219,13 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
             }
             continue;
         }
-        // ---------------- schedule: counting sort of the core's edges by circle colour
+        // ---------------- schedule: counting sort of the core's edges by circle colour,
+        // each class padded to a multiple of 4 edges with no-op edges (nH, nH)
         float* L = reinterpret_cast<float*>(sm);                         // [nH + 1]
         int32_t* start = reinterpret_cast<int32_t*>(L + nH + 1);         // [P + 1]
         int32_t* cursor = start + P + 1;                                 // [P + 1]
         const uint32_t Np = (uint32_t)(nH + (nH & 1));
+        const uint32_t sentinel = pack(nH, nH);
         for (int32_t i = tid; i <= P; i += nt) start[i] = 0;
         __syncthreads();
         auto colour = [&](uint32_t p) -> int32_t {
@@ -219,8 +234,11 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
         };
         for (int32_t e = tid; e < mH; e += nt) atomicAdd(&start[colour(cur[e])], 1);
         __syncthreads();
-        block_scan_smem(start, P + 1, red);   // start[P] = mH
-        for (int32_t i = tid; i <= P; i += nt) cursor[i] = start[i];
+        for (int32_t i = tid; i < P; i += nt) cursor[i] = start[i];      // real counts
+        for (int32_t i = tid; i <= P; i += nt) start[i] = i < P ? (start[i] + 3) & ~3 : 0;
+        __syncthreads();
+        const int32_t mHp = block_scan_smem(start, P + 1, red);          // start[P] = padded total
+        for (int32_t i = tid; i < P; i += nt) cursor[i] = start[i];
         __syncthreads();
         for (int32_t e = tid; e < mH; e += nt) {
             const uint32_t p = cur[e];
@@ -228,41 +246,187 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
             nxt[pos] = p;
             cs[pos] = 0.5f;          // Algorithm 1: f_e(u) = f_e(v) = w_e / 2
         }
+        __syncthreads();
+        for (int32_t c = tid; c < P; c += nt)
+            for (int32_t i = cursor[c]; i < start[c + 1]; ++i) { nxt[i] = sentinel; cs[i] = 0.0f; }
         __syncthreads();             // the counters below reuse `cursor`
-        // initial loads: degree in the core / 2
+        // initial loads: degree in the core / 2; slot nH is the padding edges' node
         int32_t* dH = cursor;  // reuse (P + 1 >= nH)
         for (int32_t i = tid; i < nH; i += nt) dH[i] = 0;
         __syncthreads();
-        for (int32_t e = tid; e < mH; e += nt) {
+        for (int32_t e = tid; e < mHp; e += nt) {
             const uint32_t p = nxt[e];
+            if (p == sentinel) continue;
             if ((int32_t)(p & 0xffffu) >= nH || (int32_t)(p >> 16) >= nH) { s_bad = 1; continue; }
             atomicAdd(&dH[p & 0xffffu], 1);
             atomicAdd(&dH[p >> 16], 1);
         }
         __syncthreads();
-        for (int32_t i = tid; i < nH; i += nt) L[i] = 0.5f * (float)dH[i];
+        for (int32_t i = tid; i <= nH; i += nt) L[i] = i < nH ? 0.5f * (float)dH[i] : 0.0f;
         __syncthreads();
         // ---------------- Algorithm 1 passes
-        for (int32_t t = 0; t < A.passes; ++t) {
-            for (int32_t c = 0; c < P; ++c) {
-                const int32_t beg = start[c], end = start[c + 1];
-                for (int32_t i = beg + tid; i < end; i += nt) {
-                    const uint32_t p = __ldcg(nxt + i);
-                    const int32_t a = (int32_t)(p & 0xffffu), b = (int32_t)(p >> 16);
-                    if (a >= nH || b >= nH) { s_bad = 1; continue; }   // never taken: ids checked
-                    float la = L[a], lb = L[b], s = __ldcg(cs + i);
-                    const float diff = la - lb;
-                    const bool gt = diff > 0.0f;
-                    const float cap = gt ? s : (1.0f - s);
-                    const float d = fminf(fabsf(diff) * 0.5f, cap);
-                    const float dd = gt ? d : -d;
-                    L[a] = la - dd;
-                    L[b] = lb + dd;
-                    __stcg(cs + i, fminf(s - dd, 1.0f));
+        // Staged form: chunks of G consecutive classes move global -> shared through
+        // cp.async.bulk (last warp), consumers update them in shared memory with a named
+        // barrier per class, splits go back by bulk stores.  Used when at least 3 stages of
+        // the longest chunk fit and a pass has enough chunks for the store ordering;
+        // otherwise classes are updated straight from global memory.
+        const size_t used = (((4u * (size_t)(nH + 1) + 4u * (size_t)(P + 1)) + 7) & ~(size_t)7);
+        const size_t stage_base = ((used + 16u * kBMaxStages) + 127) & ~(size_t)127;
+        if (tid < 32) {
+            // the largest chunk size G leaving room for 3 stages, then as many stages as fit
+            // and the store ordering allows (chunks per pass >= S - slack + groups + 1)
+            int32_t pick_g = 0, pick_s = 0, pick_len = 0;
+            for (int32_t g2 = 16; g2 >= 1 && mHp > 0 && nt >= 96; g2 >>= 1) {
+                int32_t mx = 0;
+                for (int32_t c0 = (int32_t)lane_id() * g2; c0 < P; c0 += 32 * g2)
+                    mx = max(mx, start[min(c0 + g2, P)] - start[c0]);
+                mx = __reduce_max_sync(0xffffffffu, mx);
+                const size_t arr = max((size_t)128, ((4u * (size_t)mx) + 127) & ~(size_t)127);
+                const int32_t fit = (int32_t)(stage_base < A.smem_bytes ? (A.smem_bytes - stage_base) / (2 * arr) : 0);
+                const int32_t NC = (P + g2 - 1) / g2;
+                const int32_t sS = min(min(fit, kBMaxStages), NC - (kBStoreGroups + 1 - kBStoreSlack));
+                if (sS >= 3) {
+                    pick_g = g2; pick_s = sS; pick_len = mx;
+                    break;
                 }
-                if (end > beg) __syncthreads();
+            }
+            if (tid == 0) { s_count = pick_g; s_rem = pick_s; s_stage_len = pick_len; }
+        }
+        fence_proxy_async_all();   // the class-major edges and splits are read by bulk copies
+        __syncthreads();
+        const int32_t G = s_count, S = s_rem, chunk_len = s_stage_len;
+        if (G > 0 && A.passes > 0) {
+            const size_t arr = max((size_t)128, ((4u * (size_t)chunk_len) + 127) & ~(size_t)127);
+            uint64_t* full = reinterpret_cast<uint64_t*>(sm + used);
+            uint64_t* empty = full + S;
+            unsigned char* stages = sm + stage_base;
+            const int nc = nt - 32;
+            if (tid == 0) {
+                s_abort = 0;
+                for (int k = 0; k < S; ++k) { mbar_init(&full[k], 1); mbar_init(&empty[k], 1); }
+                fence_mbar_init();
+                fence_proxy_async_smem();
+            }
+            __syncthreads();
+            const int32_t NC = (P + G - 1) / G;
+            const int32_t PT = NC * A.passes;     // chunks over all passes
+            const int32_t ahead = S - kBStoreSlack;
+            if (tid >= nc) {
+                if (tid == nc) {
+                    int32_t pf = 0, kf = 0, jf = 0;
+                    auto fill = [&]() {
+                        const int32_t beg = start[jf * G];
+                        const uint32_t bytes = 4u * (uint32_t)(start[min(jf * G + G, P)] - beg);
+                        unsigned char* st = stages + 2 * arr * (size_t)kf;
+                        mbar_expect_tx(&full[kf], 2u * bytes);
+                        bulk_g2s(st, nxt + beg, bytes, &full[kf]);
+                        bulk_g2s(st + arr, cs + beg, bytes, &full[kf]);
+                        ++pf;
+                        kf = (kf + 1 == S) ? 0 : kf + 1;
+                        jf = (jf + 1 == NC) ? 0 : jf + 1;
+                    };
+                    while (pf < ahead && pf < PT) fill();
+                    int32_t k = 0, j = 0;
+                    uint32_t parity = 0;
+                    int32_t q = 0;
+                    for (; q < PT; ++q) {
+                        uint32_t spins = 0;
+                        bool ok = mbar_try_wait_sleep(&empty[k], parity, 1000);
+                        while (!ok && !s_abort && ++spins < kBWaitLimit) ok = mbar_try_wait_sleep(&empty[k], parity, 1000);
+                        if (!ok) { s_abort = 1; break; }
+                        const int32_t beg = start[j * G];
+                        bulk_s2g(cs + beg, stages + 2 * arr * (size_t)k + arr,
+                                 4u * (uint32_t)(start[min(j * G + G, P)] - beg));
+                        bulk_commit();
+                        if (pf < PT) {
+                            bulk_wait<kBStoreGroups>();
+                            bulk_wait_read<kBStoreSlack>();
+                            fill();
+                        }
+                        if (++k == S) { k = 0; parity ^= 1u; }
+                        j = (j + 1 == NC) ? 0 : j + 1;
+                    }
+                    // fills [q, pf) were never handed back: on abort wait (bounded) for them
+                    if (q < PT) drain_fills(full, S, q, pf, kBWaitLimit);
+                    bulk_wait<0>();
+                }
+            } else {
+                auto wait_full = [&](int32_t kk, uint32_t par) -> bool {
+                    uint32_t spins = 0;
+                    bool ok = mbar_try_wait(&full[kk], par);
+                    while (!ok && ++spins < kBWaitLimit) ok = mbar_try_wait(&full[kk], par);
+                    return ok;
+                };
+                bool bad = false;
+                if (tid < 32 && PT > 0) bad = !wait_full(0, 0);
+                bad = consumer_sync_or(nc, bad);
+                int32_t k = 0, j = 0;
+                uint32_t parity = 0;
+                for (int32_t q = 0; q < PT && !bad; ++q) {
+                    const int32_t c0 = j * G;
+                    const int32_t c1 = min(c0 + G, P);
+                    const int32_t base = start[c0];
+                    unsigned char* st = stages + 2 * arr * (size_t)k;
+                    const uint32_t* suv = reinterpret_cast<const uint32_t*>(st);
+                    float* ss = reinterpret_cast<float*>(st + arr);
+                    int32_t cb = 0;
+                    for (int32_t c = c0; c < c1; ++c) {
+                        const int32_t ce = start[c + 1] - base;
+                        for (int32_t r = cb + tid; r < ce; r += nc) {
+                            const uint32_t p = suv[r];
+                            const int32_t a = (int32_t)(p & 0xffffu), b = (int32_t)(p >> 16);
+                            if (a > nH || b > nH) { s_bad = 1; continue; }   // never taken: ids checked
+                            const float la = L[a], lb = L[b], sv = ss[r];
+                            const float diff = la - lb;
+                            const bool gt = diff > 0.0f;
+                            const float cap = gt ? sv : (1.0f - sv);
+                            const float d = fminf(fabsf(diff) * 0.5f, cap);
+                            const float dd = gt ? d : -d;
+                            L[a] = la - dd;
+                            L[b] = lb + dd;
+                            ss[r] = fminf(sv - dd, 1.0f);
+                        }
+                        cb = ce;
+                        if (c + 1 < c1) consumer_sync(nc);
+                    }
+                    fence_proxy_async_smem();
+                    const int32_t kprev = k;
+                    if (++k == S) { k = 0; parity ^= 1u; }
+                    j = (j + 1 == NC) ? 0 : j + 1;
+                    bool fail = false;
+                    if (tid < 32 && q + 1 < PT) fail = !wait_full(k, parity);
+                    bad = consumer_sync_or(nc, fail);
+                    if (tid == 0) mbar_arrive(&empty[kprev]);
+                }
+                if (bad && tid == 0) s_abort = 1;
+            }
+            __syncthreads();
+            if (tid == 0)   // the barriers' memory is reused by the extraction and the next graph
+                for (int32_t k = 0; k < S; ++k) { mbar_inval(&full[k]); mbar_inval(&empty[k]); }
+            __syncthreads();
+        } else {
+            for (int32_t t = 0; t < A.passes; ++t) {
+                for (int32_t c = 0; c < P; ++c) {
+                    const int32_t beg = start[c], end = start[c + 1];
+                    for (int32_t i = beg + tid; i < end; i += nt) {
+                        const uint32_t p = __ldcg(nxt + i);
+                        const int32_t a = (int32_t)(p & 0xffffu), b = (int32_t)(p >> 16);
+                        if (a > nH || b > nH) { s_bad = 1; continue; }   // never taken: ids checked
+                        float la = L[a], lb = L[b], s = __ldcg(cs + i);
+                        const float diff = la - lb;
+                        const bool gt = diff > 0.0f;
+                        const float cap = gt ? s : (1.0f - s);
+                        const float d = fminf(fabsf(diff) * 0.5f, cap);
+                        const float dd = gt ? d : -d;
+                        L[a] = la - dd;
+                        L[b] = lb + dd;
+                        __stcg(cs + i, fminf(s - dd, 1.0f));
+                    }
+                    if (end > beg) __syncthreads();
+                }
             }
         }
+        for (int32_t i = tid; i < nH; i += nt) lout[oldid[i]] = L[i];
         // ---------------- extraction
         unsigned long long* keys = reinterpret_cast<unsigned long long*>(cursor + P + 1);  // [npow]
         keys = reinterpret_cast<unsigned long long*>(((uintptr_t)keys + 7) & ~(uintptr_t)7);
@@ -295,8 +459,9 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
             bucket[i] = 0;
         }
         __syncthreads();
-        for (int32_t e = tid; e < mH; e += nt) {
+        for (int32_t e = tid; e < mHp; e += nt) {
             const uint32_t p = nxt[e];
+            if (p == sentinel) continue;
             if ((int32_t)(p & 0xffffu) >= nH || (int32_t)(p >> 16) >= nH) { s_bad = 1; continue; }
             atomicAdd(&bucket[max(pos[p & 0xffffu], pos[p >> 16])], 1);
         }
@@ -328,7 +493,7 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
             s_rem = (int32_t)k2;
             A.rho[g] = k2 > 0 ? (double)W2 / (double)k2 : 0.0;
             A.S_size[g] = (int32_t)k2;
-            A.nH[g] = nH; A.mH[g] = mH; A.rounds[g] = r; A.status[g] = s_bad ? BS_BAD_INPUT : BS_OK;
+            A.nH[g] = nH; A.mH[g] = mH; A.rounds[g] = r; A.status[g] = s_bad ? BS_BAD_INPUT : (s_abort ? BS_WAIT_EXPIRED : BS_OK);
         }
         __syncthreads();
         const int32_t kstar = s_rem;
@@ -379,6 +544,7 @@ struct lowd_batch_ctx {
     double* rho = nullptr;
     int32_t *S_size = nullptr, *nH = nullptr, *mH = nullptr, *rounds = nullptr, *status = nullptr;
     uint8_t* in_S = nullptr;
+    float* loads = nullptr;
     // tuned launch
     lowd_batch_options tuned{};
     int have_tuned = 0;
@@ -408,7 +574,7 @@ void batch_free_all(lowd_batch_ctx* b) {
     if (b->own_stream && b->st) cudaStreamDestroy(b->st);
     b->st = nullptr;
     void* ps[] = {b->node_off, b->edge_off, b->u, b->v, b->eA, b->eB, b->cs, b->oldid, b->order, b->queue,
-                  b->rho, b->S_size, b->nH, b->mH, b->rounds, b->status, b->in_S};
+                  b->rho, b->S_size, b->nH, b->mH, b->rounds, b->status, b->in_S, b->loads};
     for (void* p : ps)
         if (p) cudaFree(p);
 }
@@ -472,7 +638,7 @@ cudaError_t enqueue(lowd_batch_ctx* b, const lowd_batch_options& o, int32_t coun
     A.eA = b->eA; A.eB = b->eB; A.cs = b->cs; A.oldid = b->oldid; A.order = b->order; A.queue = b->queue;
     A.passes = o.passes; A.smem_bytes = (uint32_t)cfg.smem;
     A.rho = b->rho; A.S_size = b->S_size; A.nH = b->nH; A.mH = b->mH; A.rounds = b->rounds;
-    A.status = b->status; A.in_S = b->in_S;
+    A.status = b->status; A.in_S = b->in_S; A.loads = b->loads;
     cudaError_t e = cudaMemsetAsync(b->queue, 0, sizeof(int32_t), b->st);
     if (e != cudaSuccess) return e;
     LOWD_LAUNCH(k_batch_lowd, cfg.grid, cfg.threads, cfg.smem, b->st, A);
@@ -528,9 +694,11 @@ lowd_status lowd_batch_create(int32_t B, const int64_t* node_off, const int64_t*
         if (a == cudaSuccess) a = balloc(&b->edge_off, (size_t)B + 1);
         if (a == cudaSuccess) a = balloc(&b->u, m);
         if (a == cudaSuccess) a = balloc(&b->v, m);
-        if (a == cudaSuccess) a = balloc(&b->eA, m);
-        if (a == cudaSuccess) a = balloc(&b->eB, m);
-        if (a == cudaSuccess) a = balloc(&b->cs, m);
+        // per graph: its edges plus up to 3 padding edges per colour class, 16-byte aligned
+        const size_t mp = m + 4 * n + 16;
+        if (a == cudaSuccess) a = balloc(&b->eA, mp);
+        if (a == cudaSuccess) a = balloc(&b->eB, mp);
+        if (a == cudaSuccess) a = balloc(&b->cs, mp);
         if (a == cudaSuccess) a = balloc(&b->oldid, n);
         if (a == cudaSuccess) a = balloc(&b->order, (size_t)B);
         if (a == cudaSuccess) a = balloc(&b->queue, 16);
@@ -541,6 +709,7 @@ lowd_status lowd_batch_create(int32_t B, const int64_t* node_off, const int64_t*
         if (a == cudaSuccess) a = balloc(&b->rounds, (size_t)B);
         if (a == cudaSuccess) a = balloc(&b->status, (size_t)B);
         if (a == cudaSuccess) a = balloc(&b->in_S, n);
+        if (a == cudaSuccess) a = balloc(&b->loads, n);
         if (a != cudaSuccess) s = b->fail(a);
     }
     if (s == LOWD_OK) {
@@ -592,9 +761,7 @@ lowd_status lowd_batch_run(lowd_batch b, const lowd_batch_options* opt) {
         e = prepare(o, b->B, &cfg);
         if (e != cudaSuccess) {
             lowd_status st = b->fail(e);
-            char tmp[200];
-            snprintf(tmp, sizeof(tmp), "prepare: %s", b->err);
-            snprintf(b->err, sizeof(b->err), "%s", tmp);
+            snprintf(b->err, sizeof(b->err), "prepare: %s", cudaGetErrorString(e));
             return st;
         }
         // capture the launch (queue reset + persistent kernel) once, replay it afterwards
@@ -609,9 +776,7 @@ lowd_status lowd_batch_run(lowd_batch b, const lowd_batch_options* opt) {
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
             lowd_status st = b->fail(e);
-            char tmp[200];
-            snprintf(tmp, sizeof(tmp), "capture: %s", b->err);
-            snprintf(b->err, sizeof(b->err), "%s", tmp);
+            snprintf(b->err, sizeof(b->err), "capture: %s", cudaGetErrorString(e));
             return st;
         }
         b->gopt = o;
@@ -681,6 +846,15 @@ lowd_status lowd_batch_results(lowd_batch b, double* rho, int32_t* S_size, uint8
     if (m_core && e == cudaSuccess) e = cudaMemcpyAsync(m_core, b->mH, sizeof(int32_t) * B, k, b->st);
     if (rounds && e == cudaSuccess) e = cudaMemcpyAsync(rounds, b->rounds, sizeof(int32_t) * B, k, b->st);
     if (status && e == cudaSuccess) e = cudaMemcpyAsync(status, b->status, sizeof(int32_t) * B, k, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return b->fail(e);
+    return LOWD_OK;
+}
+
+lowd_status lowd_batch_loads(lowd_batch b, float* loads) {
+    if (!b || !loads) return LOWD_ERR_INVALID_ARG;
+    const cudaMemcpyKind k = b->mem == LOWD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpyAsync(loads, b->loads, sizeof(float) * (size_t)b->n_total, k, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return b->fail(e);
     return LOWD_OK;

@@ -35,7 +35,7 @@ EXPORTED = (
     "lowd_get_prune_info", "lowd_get_edge_order", "lowd_free", "lowd_status_string",
     "lowd_last_error", "lowd_launch_count", "lowd_extract_noalloc",
     "lowd_batch_create", "lowd_batch_run", "lowd_batch_autotune", "lowd_batch_results",
-    "lowd_batch_free", "lowd_batch_last_error", "lowd_get_ldd",
+    "lowd_batch_free", "lowd_batch_last_error", "lowd_batch_loads", "lowd_get_ldd",
 )
 LOWD_BATCH_ORDER_AS_GIVEN = 1
 LOWD_BATCH_ORDER_LARGEST_FIRST = 2
@@ -125,6 +125,8 @@ def load_library(path: str = LIB_PATH):
     lib.lowd_batch_autotune.argtypes = [P, i32, i32, C.POINTER(lowd_batch_options)]
     lib.lowd_batch_results.restype = i32
     lib.lowd_batch_results.argtypes = [P, P, P, P, P, P, P, P]
+    lib.lowd_batch_loads.restype = i32
+    lib.lowd_batch_loads.argtypes = [P, P]
     lib.lowd_batch_last_error.restype = C.c_char_p
     lib.lowd_batch_last_error.argtypes = [P]
     lib.lowd_batch_free.restype = None
@@ -405,6 +407,15 @@ def lowd_batch_results(b: Batch) -> dict:
     if s != LOWD_OK:
         raise LowdError(s, "lowd_batch_results")
     return dict(rho=rho, S_size=size, in_S=ins[:b.n_total], n_core=nc, m_core=mc, rounds=rr, status=st)
+
+
+def lowd_batch_loads(b: Batch) -> np.ndarray:
+    """FP32 loads after the last run's passes, all graphs' nodes by local id."""
+    out = np.empty(max(b.n_total, 1), np.float32)
+    s = load_library().lowd_batch_loads(b.ptr, out.ctypes.data_as(C.c_void_p))
+    if s != LOWD_OK:
+        raise LowdError(s, "lowd_batch_loads", load_library().lowd_batch_last_error(b.ptr).decode())
+    return out[:b.n_total]
 
 
 def lowd_batch_free(b: Batch):

@@ -1,7 +1,8 @@
 """Batched LOWD (many graphs, one persistent launch) against the oracle, graph by graph.
 
 Per graph: the pruning rounds and the pruned core's size (bit-exact against Algorithm 2 in
-the oracle), and after 300 passes the densest set and density against the exact min-cut
+the oracle); after 1 and 9 passes the loads against the FP64 oracle replaying the
+circle-colouring classes of its own pruned core; after 300 passes the densest set and density against the exact min-cut
 solution (S* equal to the maximal densest set B_1, rho* within 1e-9 relative).  Also: the
 autotuned and the captured-graph replays give the same results, and non-canonical input is
 refused.
@@ -10,6 +11,7 @@ import numpy as np
 import pytest
 
 import synth
+from _oracle_side import oracle_graph
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +38,7 @@ def setup():
         keep = pr["removal_round"] < 0
         rho, B1 = oracle.densest_flow(g.n, g.u, g.v, wu)
         ref.append(dict(rounds=pr["rounds"], n_core=int(keep.sum()),
-                        m_core=int((keep[g.u] & keep[g.v]).sum()), rho=float(rho), B1=B1))
+                        m_core=int((keep[g.u] & keep[g.v]).sum()), rho=float(rho), B1=B1, keep=keep))
     return pkg, graphs, node_off, edge_off, u, v, ref
 
 
@@ -65,6 +67,29 @@ def test_batch_matches_oracle(setup):
     assert best["ctas_per_sm"] in (1, 2) and best["threads"] in (256, 512, 1024)
     pkg.lowd_batch_run(b, passes=300)
     _check(pkg.lowd_batch_results(b), graphs, node_off, ref)
+    pkg.lowd_batch_free(b)
+
+
+@pytest.mark.parametrize("T", [1, 9])
+def test_batch_same_order_loads(setup, T):
+    """Loads after T passes: the oracle prunes, compacts and orders the core itself."""
+    import oracle as orc
+    pkg, graphs, node_off, edge_off, u, v, ref = setup
+    b = pkg.lowd_batch_create(node_off, edge_off, u, v)
+    for thr in (256, 1024):
+        pkg.lowd_batch_run(b, passes=T, threads=thr)
+        res = pkg.lowd_batch_results(b)
+        lg = pkg.lowd_batch_loads(b)
+        for i, g in enumerate(graphs):
+            assert res["status"][i] == 0, i
+            nh, uh, vh, _, idmap = oracle_graph(orc, g, True)
+            order, _, _ = orc.circle_order(nh, uh, vh)
+            o = orc.LowdState(nh, uh, vh)
+            o.iterate(T, order=order)
+            li = lg[node_off[i]:node_off[i + 1]].astype(np.float64)
+            assert np.all(li[~ref[i]["keep"]] == 0), i
+            err = np.max(np.abs(li[idmap] - o.l)) if nh else 0.0
+            assert err <= 1e-4 * max(1.0, o.l.max() if nh else 1.0), (i, T, thr, err)
     pkg.lowd_batch_free(b)
 
 

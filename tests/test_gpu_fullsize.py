@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import synth
+from _oracle_side import assert_same_schedule
 
 pytestmark = pytest.mark.gpu
 
@@ -53,9 +54,9 @@ def test_rmat22_prune_core_and_passes(setup):
     assert (nk, mk) == (nh, uh.shape[0])
     assert np.array_equal(gu, uh) and np.array_equal(gv, vh)
 
-    # two passes, replayed in the GPU's order by the FP64 oracle
+    # two passes; the FP64 oracle replays its own colour-class order (the GPU's classes)
     st1 = pkg.lowd_iterate(h, 1)
-    order = pkg.lowd_get_edge_order(h)[0].cpu().numpy()
+    order = assert_same_schedule(orc, nh, uh, vh, *(x.cpu().numpy() for x in pkg.lowd_get_edge_order(h)))
     st2 = pkg.lowd_iterate(h, 1)
     o = orc.LowdState(nh, uh, vh)
     o.iterate(2, order=order)

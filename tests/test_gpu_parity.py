@@ -5,7 +5,8 @@ Bars (bit-exact where the work is integer, tolerance where it is floating point)
    bit-exact;
  - extraction: the GPU's S* and W(S*) equal the oracle's extraction run on the same FP32
    loads (the order decision is taken in FP32 on both sides), bit-exact;
- - same-order LOWD: the oracle (FP64) replays the GPU's edge order; loads agree within
+ - same-order LOWD: the GPU's classes must be the oracle's circle-colouring classes in
+   the oracle's order; the oracle (FP64) replays its own order; loads agree within
    LOAD_TOL * max load, the tolerance derived for FP32 passes;
  - converged: loads within 1e-4 relative of the exact LDD loads, S* equal to the maximal
    densest set from the min-cut solver, rho* within 1e-9 relative.
@@ -14,6 +15,7 @@ import numpy as np
 import pytest
 
 import synth
+from _oracle_side import assert_same_schedule, oracle_graph
 
 pytestmark = pytest.mark.gpu
 
@@ -167,15 +169,18 @@ def _same_order(pkg, orc, g, prune, T, device=True):
     h = _load(pkg, g, device)
     if prune:
         pkg.lowd_prune(h)
-    gu, gv, gw = pkg.lowd_get_graph(h)
-    gu, gv, gw = _np(gu), _np(gv), _np(gw)
+    n, u, v, w, _ = oracle_graph(orc, g, prune)
+    gu, gv, gw = (_np(x) for x in pkg.lowd_get_graph(h))
+    assert np.array_equal(gu, u) and np.array_equal(gv, v)
     info = pkg.lowd_get_info(h)
+    assert info["n"] == n
     pkg.lowd_iterate(h, T)
     perm, offs = pkg.lowd_get_edge_order(h)
     perm, offs = _np(perm), _np(offs)
-    o = orc.LowdState(info["n"], gu, gv, None if g.w is None else gw.astype(np.float64))
-    o.iterate(T, order=perm)
-    return h, o, perm, offs, (gu, gv, gw), info
+    order = assert_same_schedule(orc, n, u, v, perm, offs)
+    o = orc.LowdState(n, u, v, w)
+    o.iterate(T, order=order)
+    return h, o, perm, offs, (u, v, w), info
 
 
 @pytest.mark.parametrize("name,prune,T", [
@@ -184,7 +189,7 @@ def _same_order(pkg, orc, g, prune, T, device=True):
 ])
 def test_same_order_loads(pkg, orc, name, prune, T):
     g = _graph(name, False if name != "planted" else False)
-    h, o, perm, offs, (gu, gv, gw), info = _same_order(pkg, orc, g, prune, T)
+    h, o, perm, offs, (gu, gv, _), info = _same_order(pkg, orc, g, prune, T)
     # the schedule is a permutation whose classes are matchings
     assert np.array_equal(np.sort(perm), np.arange(info["m"]))
     for c in range(offs.shape[0] - 1):
@@ -208,15 +213,16 @@ def test_same_order_weighted_and_sumsq(pkg, orc, weighted):
         g.w = synth.quantise_weights(np.random.default_rng(8).lognormal(0, 1, g.m))
     h = _load(pkg, g, True)
     pkg.lowd_prune(h)
+    n, u, v, w, _ = oracle_graph(orc, g, True)
     gu, gv, gw = (_np(x) for x in pkg.lowd_get_graph(h))
-    info = pkg.lowd_get_info(h)
-    o = orc.LowdState(info["n"], gu, gv, None if g.w is None else gw.astype(np.float64))
+    assert np.array_equal(gu, u) and np.array_equal(gv, v)
+    o = orc.LowdState(n, u, v, w)
     prev = None
     for t in range(12):
         st = pkg.lowd_iterate(h, 5)
         if t == 0:
-            perm = _np(pkg.lowd_get_edge_order(h)[0])
-        o.iterate(5, order=perm)
+            order = assert_same_schedule(orc, n, u, v, *(_np(x) for x in pkg.lowd_get_edge_order(h)))
+        o.iterate(5, order=order)
         lg = _np(pkg.lowd_get_loads(h)).astype(np.float64)
         assert np.max(np.abs(lg - o.l)) <= LOAD_TOL * max(1.0, o.l.max())
         # sum of squared loads falls monotonically (Sec. III-C), up to FP32 rounding
