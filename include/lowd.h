@@ -193,6 +193,23 @@ lowd_status lowd_extract(lowd_handle h, int32_t* S, int32_t* S_size, double* rho
 lowd_status lowd_get_ldd(lowd_handle h, double rel_tol, int32_t* shell, double* lambda,
                          int32_t* shell_end, int32_t* n_shells);
 
+/*
+ * lowd_ldd_dks_bound - Corollary 1 on an exported decomposition: the upper bound on the
+ * density of any k-node subgraph (DkS) and of any subgraph with at least k nodes (DalkS)
+ * of the graph the decomposition was taken on.  With |B_{j-1}| < k <= |B_j|,
+ *     bound = (W(B_{j-1}) + (k - |B_{j-1}|) * lambda_j) / k,
+ * W(B_{j-1}) = sum_{i<j} lambda_i * |B_i \ B_{i-1}|: the mean of the k largest loads (the
+ * corollary's proof bounds W(S) by the loads of S; its sum over lambda_i * |B_i| counts
+ * each shell's own nodes, |B_i \ B_{i-1}|).  For k = |B_j| the bound is attained by B_j
+ * (Corollary 1, item 1) and *exact is set to 1.  Host arithmetic, no GPU work.
+ *   n_shells, shell_end, lambda   host arrays as returned by lowd_get_ldd
+ *   k          1 <= k <= shell_end[n_shells - 1], else LOWD_ERR_INVALID_ARG
+ *   bound      host out; exact: host out (may be NULL)
+ * Taken after lowd_prune, the decomposition and the bound are those of the pruned graph.
+ */
+lowd_status lowd_ldd_dks_bound(int32_t n_shells, const int32_t* shell_end, const double* lambda, int32_t k,
+                               double* bound, int32_t* exact);
+
 /* Current graph sizes and schedule.  info: host pointer. */
 lowd_status lowd_get_info(lowd_handle h, lowd_info* info);
 

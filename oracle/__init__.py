@@ -290,6 +290,27 @@ def ldd_loads(n, u, v, wu, scale: int = 1):
     return lamf[shell - 1] if n else np.zeros(0), shell, lam
 
 
+def dks_bound(n, u, v, wu, k: int):
+    """Corollary 1 from the exact decomposition: with |B_{j-1}| < k <= |B_j|, the bound
+    (W(B_{j-1}) + (k - |B_{j-1}|) lambda_j) / k on the densest k-subgraph and at-least-k
+    subgraph densities (reading: the corollary's lambda_i * |B_i| is lambda_i times the
+    size of shell i, as its proof sums the loads of the k heaviest nodes).  Returns
+    (Fraction in weight units, attained) where attained means k = |B_j|.
+
+    Parity pinned by tests/test_oracle_dks.py against brute-force DkS and DalkS."""
+    shell, lam = ldd(n, u, v, wu)
+    sizes = np.bincount(shell, minlength=len(lam) + 1)[1:]
+    if not 1 <= k <= int(sizes.sum()):
+        raise ValueError("k out of range")
+    prefix, prev = Fraction(0), 0
+    for j, (sz, lj) in enumerate(zip(sizes.tolist(), lam)):
+        if k <= prev + sz:
+            return (prefix + (k - prev) * lj) / k, k == prev + sz
+        prefix += lj * sz
+        prev += sz
+    raise AssertionError("unreachable")
+
+
 # ----------------------------------------------------------------------------- full pipeline
 
 def solve(n, u, v, w=None, T: int = 100, prune_first: bool = True, order=None):

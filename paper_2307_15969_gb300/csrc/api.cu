@@ -239,6 +239,25 @@ lowd_status lowd_extract(lowd_handle h, int32_t* S, int32_t* S_size, double* rho
     return s;
 }
 
+lowd_status lowd_ldd_dks_bound(int32_t n_shells, const int32_t* shell_end, const double* lambda, int32_t k,
+                               double* bound, int32_t* exact) {
+    if (n_shells < 1 || !shell_end || !lambda || !bound || k < 1 || k > shell_end[n_shells - 1])
+        return LOWD_ERR_INVALID_ARG;
+    double prefix = 0.0;   // W(B_{j-1})
+    int32_t prev = 0;      // |B_{j-1}|
+    for (int32_t j = 0; j < n_shells; ++j) {
+        if (shell_end[j] <= prev) return LOWD_ERR_INVALID_ARG;   // sizes must grow
+        if (k <= shell_end[j]) {
+            *bound = (prefix + (double)(k - prev) * lambda[j]) / (double)k;
+            if (exact) *exact = k == shell_end[j] ? 1 : 0;
+            return LOWD_OK;
+        }
+        prefix += lambda[j] * (double)(shell_end[j] - prev);
+        prev = shell_end[j];
+    }
+    return LOWD_ERR_INVALID_ARG;
+}
+
 lowd_status lowd_get_ldd(lowd_handle h, double rel_tol, int32_t* shell, double* lambda, int32_t* shell_end,
                          int32_t* n_shells) {
     LOWD_TRY(check_handle(h));

@@ -36,6 +36,7 @@ EXPORTED = (
     "lowd_last_error", "lowd_launch_count", "lowd_extract_noalloc",
     "lowd_batch_create", "lowd_batch_run", "lowd_batch_autotune", "lowd_batch_results",
     "lowd_batch_free", "lowd_batch_last_error", "lowd_batch_loads", "lowd_get_ldd",
+    "lowd_ldd_dks_bound",
 )
 LOWD_BATCH_ORDER_AS_GIVEN = 1
 LOWD_BATCH_ORDER_LARGEST_FIRST = 2
@@ -95,6 +96,8 @@ def load_library(path: str = LIB_PATH):
     lib.lowd_extract.argtypes = [P, P, C.POINTER(i32), C.POINTER(C.c_double), P]
     lib.lowd_get_ldd.restype = i32
     lib.lowd_get_ldd.argtypes = [P, C.c_double, P, P, P, C.POINTER(i32)]
+    lib.lowd_ldd_dks_bound.restype = i32
+    lib.lowd_ldd_dks_bound.argtypes = [i32, P, P, i32, C.POINTER(C.c_double), C.POINTER(i32)]
     lib.lowd_get_info.restype = i32
     lib.lowd_get_info.argtypes = [P, C.POINTER(lowd_info)]
     lib.lowd_get_graph.restype = i32
@@ -276,6 +279,20 @@ def lowd_get_ldd(h: Handle, rel_tol: float = 1e-5):
     h._check(load_library().lowd_get_ldd(h.ptr, float(rel_tol), h.ptr_of(shell), lamp, h.ptr_of(end),
                                          C.byref(ns)), "lowd_get_ldd")
     return shell[:h.n0], lam[:ns.value], end[:ns.value]
+
+
+def lowd_ldd_dks_bound(lam, shell_end, k: int):
+    """Corollary 1: (upper bound on the k-subgraph / at-least-k subgraph density, whether
+    it is attained, i.e. k = |B_j|), from lowd_get_ldd's lambda and shell_end."""
+    lam = np.ascontiguousarray(lam.cpu().numpy() if hasattr(lam, "cpu") else lam, np.float64)
+    end = np.ascontiguousarray(shell_end.cpu().numpy() if hasattr(shell_end, "cpu") else shell_end, np.int32)
+    b = C.c_double()
+    ex = i32()
+    s = load_library().lowd_ldd_dks_bound(int(lam.shape[0]), end.ctypes.data_as(C.c_void_p),
+                                          lam.ctypes.data_as(C.c_void_p), int(k), C.byref(b), C.byref(ex))
+    if s != LOWD_OK:
+        raise LowdError(s, "lowd_ldd_dks_bound")
+    return b.value, bool(ex.value)
 
 
 def lowd_get_info(h: Handle) -> dict:

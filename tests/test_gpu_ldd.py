@@ -3,7 +3,8 @@
 On graphs whose exact shell loads are separated by more than the grouping tolerance, after
 enough passes for the loads to converge (Theorem 2), every node's shell equals the one from
 the oracle's min-cut decomposition (Sec. II, Definition of LDD) and each lambda_i equals the
-exact shell density (Property 2) to double precision.
+exact shell density (Property 2) to double precision; Corollary 1's DkS/DalkS bounds read
+off the export equal the oracle's.
 """
 import numpy as np
 import pytest
@@ -55,6 +56,11 @@ def test_ldd_export_matches_exact_decomposition(setup):
         assert np.allclose(lam_g, lf, rtol=1e-12, atol=0), g.name
         sizes = np.bincount(shell)[1:]
         assert np.array_equal(end.cpu().numpy(), np.cumsum(sizes)), g.name
+        # Corollary 1 bounds from the exported decomposition against the oracle's
+        for k in range(1, g.n + 1, max(1, g.n // 50)):
+            b, ex = pkg.lowd_ldd_dks_bound(lam_g, end, k)
+            bo, exo = orc.dks_bound(g.n, g.u, g.v, wu, k)
+            assert ex == exo and abs(b - float(bo) / scale) <= 1e-12 * float(bo) / scale, (g.name, k)
         pkg.lowd_free(h)
         tested += 1
     assert tested >= 3
