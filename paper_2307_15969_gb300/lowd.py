@@ -287,7 +287,7 @@ def lowd_ldd_dks_bound(lam, shell_end, k: int):
     lam = np.ascontiguousarray(lam.cpu().numpy() if hasattr(lam, "cpu") else lam, np.float64)
     end = np.ascontiguousarray(shell_end.cpu().numpy() if hasattr(shell_end, "cpu") else shell_end, np.int32)
     b = C.c_double()
-    ex = i32()
+    ex = C.c_int32()
     s = load_library().lowd_ldd_dks_bound(int(lam.shape[0]), end.ctypes.data_as(C.c_void_p),
                                           lam.ctypes.data_as(C.c_void_p), int(k), C.byref(b), C.byref(ex))
     if s != LOWD_OK:
