@@ -332,6 +332,67 @@ const char* lowd_batch_last_error(lowd_batch b);
 
 void lowd_batch_free(lowd_batch b);
 
+/* ------------------------------------------------------------------ learned warm start
+ *
+ * Not in the paper: the paper starts every edge at the equal split f_e(u) = f_e(v) = w_e/2
+ * (Algorithm 1's initialisation).  Any split inside [0, w_e] is a valid start - the
+ * convergence argument of Theorem 2 does not depend on it - so a start closer to the
+ * optimum only saves passes; the passes, the stop test and the extraction are unchanged.
+ * The predictor is a mean-aggregation message-passing network (hidden width 64, three
+ * layers; BF16 node states and layer weights, FP32 accumulation, the layer products on the
+ * tensor cores) on the graph the passes run on:
+ *   x_v   = (log(1 + d_v), mean of log w_e over v's edges, log(1 + sum of the neighbours'
+ *            d)), d_v = weighted degree
+ *   h0    = relu(x W_in + b_in);  per layer: m_v = mean of h over v's neighbours,
+ *           h' = relu([h, m] W_l^T + b_l)
+ *   phi_v = q . h3_v;  sigma_e = 1 / (1 + exp(phi_hi - phi_lo));  f_e(lo) = sigma_e w_e
+ * Training loss (lowd_mpnn_forward with a target): sum_v (l_v - t_v)^2 / sum_v t_v^2,
+ * l_v the loads of the predicted splits, t_v target loads (converged LOWD loads).
+ * Flat FP32 parameter vector of lowd_mpnn_param_count() entries: W_in [3][64] (row-major
+ * [in][out]), b_in [64], then per layer W_l [64][128] ([out][in]) and b_l [64], then q [64].
+ */
+typedef struct lowd_mpnn_ctx* lowd_mpnn;
+
+enum { LOWD_MPNN_SIGMA = 1, LOWD_MPNN_LOADS = 2, LOWD_MPNN_GRAD = 3, LOWD_MPNN_FEATURES = 4, LOWD_MPNN_PHI = 5 };
+
+int64_t lowd_mpnn_param_count(void);
+
+/* A network with all parameters 0 (every predicted split is the equal split) and its own
+ * device state; stream as in lowd_batch_create (NULL: a non-blocking stream of its own). */
+lowd_status lowd_mpnn_create(void* stream, lowd_mpnn* out);
+
+/* Copy the FP32 parameters in (host or device per mem); resets the Adam state. */
+lowd_status lowd_mpnn_set_params(lowd_mpnn net, const float* params, int32_t mem);
+lowd_status lowd_mpnn_get_params(lowd_mpnn net, float* params, int32_t mem);
+
+/* Bind a graph (copied): n nodes, m edges lo[e] < hi[e] < n, each pair once; w [m] > 0 or
+ * NULL for unit weights; target [n] loads or NULL.  Builds the adjacency and the input
+ * features.  m < 2^30.  LOWD_ERR_INVALID_ARG on an edge or weight outside these rules. */
+lowd_status lowd_mpnn_bind(lowd_mpnn net, int32_t n, int64_t m, const int32_t* lo, const int32_t* hi,
+                           const float* w, const float* target, int32_t mem);
+
+/* Forward pass on the bound graph: splits sigma, their loads and, with a target, the loss
+ * (loss may be NULL; a non-NULL loss without a target is LOWD_ERR_BAD_STATE). */
+lowd_status lowd_mpnn_forward(lowd_mpnn net, double* loss);
+
+/* Gradient of the loss of the last forward pass with respect to every parameter. */
+lowd_status lowd_mpnn_backward(lowd_mpnn net);
+
+/* One Adam step (bias-corrected, step counter kept by the network) with the last gradient. */
+lowd_status lowd_mpnn_adam(lowd_mpnn net, float lr, float beta1, float beta2, float eps);
+
+/* Read LOWD_MPNN_SIGMA [m], LOADS [n], PHI [n] (after a forward pass), FEATURES [3n] (after
+ * bind) or GRAD [param_count] into out (host or device per mem). */
+lowd_status lowd_mpnn_read(lowd_mpnn net, int32_t what, float* out, int32_t mem);
+
+/* Warm start of a handle: the network's splits on the handle's current graph (G, or H
+ * after lowd_prune) become the LOWD state, s_e = sigma_e w_e; before the first lowd_iterate
+ * this replaces the equal split, later it replaces the current splits (loads re-derived). */
+lowd_status lowd_warm_start(lowd_handle h, lowd_mpnn net);
+
+const char* lowd_mpnn_last_error(lowd_mpnn net);
+void lowd_mpnn_free(lowd_mpnn net);
+
 /* Release the handle and all its device memory.  NULL is ignored. */
 void lowd_free(lowd_handle h);
 

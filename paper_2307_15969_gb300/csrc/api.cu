@@ -344,32 +344,36 @@ lowd_status lowd_get_splits(lowd_handle h, float* s) {
     return r;
 }
 
+}  // extern "C"
+
+// Splits (canonical order, device) become the state: the first time they initialise the
+// schedule, later they replace the splits (clamped to [0, w_e]) and the loads are
+// re-derived from them.
+lowd_status lowd_apply_splits_dev(lowd_ctx* h, const float* d) {
+    if (!h->inited) return lowd_sweep_prepare(h, 0, d);
+    float* c = nullptr;
+    LOWD_TRY(dalloc(h, &c, h->m));
+    if (h->m > 0) LOWD_LAUNCH(k_clamp_splits, grid_for(h->m), 256, 0, h->st, d, h->w, h->m, c);
+    lowd_status r = lowd_sweep_load_canonical(h, c);
+    cudaStreamSynchronize(h->st);
+    dfree(&c);
+    if (r) return r;
+    double st3[3];
+    return lowd_sweep_rederive(h, st3);
+}
+
+extern "C" {
+
 lowd_status lowd_set_splits(lowd_handle h, const float* s) {
     LOWD_TRY(check_handle(h));
     if (!s) return LOWD_ERR_INVALID_ARG;
     float* d = nullptr;
     LOWD_TRY(dalloc(h, &d, h->m));
     lowd_status r = LOWD_OK;
-    do {
-        cudaMemcpyKind k = h->mem == LOWD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        if (h->m > 0 && cudaMemcpyAsync(d, s, sizeof(float) * (size_t)h->m, k, h->st) != cudaSuccess) {
-            r = h->fail(cudaGetLastError());
-            break;
-        }
-        if (!h->inited) {
-            r = lowd_sweep_prepare(h, 0, d);
-        } else {
-            float* c = nullptr;
-            if ((r = dalloc(h, &c, h->m))) break;
-            if (h->m > 0) LOWD_LAUNCH(k_clamp_splits, grid_for(h->m), 256, 0, h->st, d, h->w, h->m, c);
-            r = lowd_sweep_load_canonical(h, c);
-            cudaStreamSynchronize(h->st);
-            dfree(&c);
-            if (r) break;
-            double st3[3];
-            r = lowd_sweep_rederive(h, st3);
-        }
-    } while (0);
+    cudaMemcpyKind k = h->mem == LOWD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (h->m > 0 && cudaMemcpyAsync(d, s, sizeof(float) * (size_t)h->m, k, h->st) != cudaSuccess)
+        r = h->fail(cudaGetLastError());
+    if (r == LOWD_OK) r = lowd_apply_splits_dev(h, d);
     cudaStreamSynchronize(h->st);
     dfree(&d);
     return r;

@@ -132,6 +132,9 @@ lowd_status lowd_sweep_splits_canonical(lowd_ctx* h, float* out_dev);
 lowd_status lowd_sweep_load_canonical(lowd_ctx* h, const float* splits_dev);
 lowd_status lowd_sweep_edge_order(lowd_ctx* h, int32_t* out_dev);
 
+// api.cu
+lowd_status lowd_apply_splits_dev(lowd_ctx* h, const float* splits_canon_dev);
+
 // extract.cu
 lowd_status lowd_extract_best(lowd_ctx* h, const float* loads_dev, int32_t* S_dev_current,
                               int32_t* S_size, int64_t* W_best);

@@ -36,8 +36,15 @@ EXPORTED = (
     "lowd_last_error", "lowd_launch_count", "lowd_extract_noalloc",
     "lowd_batch_create", "lowd_batch_run", "lowd_batch_autotune", "lowd_batch_results",
     "lowd_batch_free", "lowd_batch_last_error", "lowd_batch_loads", "lowd_get_ldd",
-    "lowd_ldd_dks_bound",
+    "lowd_ldd_dks_bound", "lowd_mpnn_param_count", "lowd_mpnn_create", "lowd_mpnn_set_params",
+    "lowd_mpnn_get_params", "lowd_mpnn_bind", "lowd_mpnn_forward", "lowd_mpnn_backward", "lowd_mpnn_adam",
+    "lowd_mpnn_read", "lowd_warm_start", "lowd_mpnn_last_error", "lowd_mpnn_free",
 )
+LOWD_MPNN_SIGMA = 1
+LOWD_MPNN_LOADS = 2
+LOWD_MPNN_GRAD = 3
+LOWD_MPNN_FEATURES = 4
+LOWD_MPNN_PHI = 5
 LOWD_BATCH_ORDER_AS_GIVEN = 1
 LOWD_BATCH_ORDER_LARGEST_FIRST = 2
 
@@ -98,6 +105,30 @@ def load_library(path: str = LIB_PATH):
     lib.lowd_get_ldd.argtypes = [P, C.c_double, P, P, P, C.POINTER(i32)]
     lib.lowd_ldd_dks_bound.restype = i32
     lib.lowd_ldd_dks_bound.argtypes = [i32, P, P, i32, C.POINTER(C.c_double), C.POINTER(i32)]
+    lib.lowd_mpnn_param_count.restype = C.c_int64
+    lib.lowd_mpnn_param_count.argtypes = []
+    lib.lowd_mpnn_create.restype = i32
+    lib.lowd_mpnn_create.argtypes = [P, C.POINTER(C.c_void_p)]
+    lib.lowd_mpnn_set_params.restype = i32
+    lib.lowd_mpnn_set_params.argtypes = [P, P, i32]
+    lib.lowd_mpnn_get_params.restype = i32
+    lib.lowd_mpnn_get_params.argtypes = [P, P, i32]
+    lib.lowd_mpnn_bind.restype = i32
+    lib.lowd_mpnn_bind.argtypes = [P, i32, C.c_int64, P, P, P, P, i32]
+    lib.lowd_mpnn_forward.restype = i32
+    lib.lowd_mpnn_forward.argtypes = [P, C.POINTER(C.c_double)]
+    lib.lowd_mpnn_backward.restype = i32
+    lib.lowd_mpnn_backward.argtypes = [P]
+    lib.lowd_mpnn_adam.restype = i32
+    lib.lowd_mpnn_adam.argtypes = [P, C.c_float, C.c_float, C.c_float, C.c_float]
+    lib.lowd_mpnn_read.restype = i32
+    lib.lowd_mpnn_read.argtypes = [P, i32, P, i32]
+    lib.lowd_warm_start.restype = i32
+    lib.lowd_warm_start.argtypes = [P, P]
+    lib.lowd_mpnn_last_error.restype = C.c_char_p
+    lib.lowd_mpnn_last_error.argtypes = [P]
+    lib.lowd_mpnn_free.restype = None
+    lib.lowd_mpnn_free.argtypes = [P]
     lib.lowd_get_info.restype = i32
     lib.lowd_get_info.argtypes = [P, C.POINTER(lowd_info)]
     lib.lowd_get_graph.restype = i32
@@ -439,3 +470,104 @@ def lowd_batch_free(b: Batch):
     if b is not None and b.ptr and b.ptr.value:
         load_library().lowd_batch_free(b.ptr)
         b.ptr = C.c_void_p(None)
+
+
+# ----------------------------------------------------------------------------- warm-start network
+
+class Mpnn:
+    """The warm-start network (the C ``lowd_mpnn``); host-mode arrays (numpy)."""
+
+    def __init__(self, ptr: int):
+        self.ptr = C.c_void_p(ptr)
+        self.n = 0
+        self.m = 0
+
+    def __del__(self):
+        try:
+            lowd_mpnn_free(self)
+        except Exception:
+            pass
+
+    def _check(self, status: int, where: str):
+        if status != LOWD_OK:
+            detail = load_library().lowd_mpnn_last_error(self.ptr).decode() if self.ptr else ""
+            raise LowdError(status, where, detail)
+
+
+def _f32p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def lowd_mpnn_param_count() -> int:
+    return int(load_library().lowd_mpnn_param_count())
+
+
+def lowd_mpnn_create(stream=None) -> Mpnn:
+    out = C.c_void_p()
+    sptr = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    s = load_library().lowd_mpnn_create(sptr, C.byref(out))
+    if s != LOWD_OK:
+        raise LowdError(s, "lowd_mpnn_create")
+    return Mpnn(out.value)
+
+
+def lowd_mpnn_set_params(net: Mpnn, params):
+    p = np.ascontiguousarray(params, np.float32)
+    if p.shape[0] != lowd_mpnn_param_count():
+        raise ValueError("wrong parameter count")
+    net._check(load_library().lowd_mpnn_set_params(net.ptr, _f32p(p), LOWD_MEM_HOST), "lowd_mpnn_set_params")
+
+
+def lowd_mpnn_get_params(net: Mpnn) -> np.ndarray:
+    p = np.empty(lowd_mpnn_param_count(), np.float32)
+    net._check(load_library().lowd_mpnn_get_params(net.ptr, _f32p(p), LOWD_MEM_HOST), "lowd_mpnn_get_params")
+    return p
+
+
+def lowd_mpnn_bind(net: Mpnn, n: int, lo, hi, w=None, target=None):
+    lo = np.ascontiguousarray(lo, np.int32)
+    hi = np.ascontiguousarray(hi, np.int32)
+    m = int(lo.shape[0])
+    if hi.shape[0] != m:
+        raise ValueError("lo, hi must have the same length")
+    wa = None if w is None else np.ascontiguousarray(w, np.float32)
+    ta = None if target is None else np.ascontiguousarray(target, np.float32)
+    s = load_library().lowd_mpnn_bind(net.ptr, int(n), m, _f32p(lo), _f32p(hi),
+                                      None if wa is None else _f32p(wa), None if ta is None else _f32p(ta),
+                                      LOWD_MEM_HOST)
+    net._check(s, "lowd_mpnn_bind")
+    net.n, net.m = int(n), m
+
+
+def lowd_mpnn_forward(net: Mpnn, with_loss: bool = True):
+    loss = C.c_double()
+    net._check(load_library().lowd_mpnn_forward(net.ptr, C.byref(loss) if with_loss else None), "lowd_mpnn_forward")
+    return loss.value if with_loss else None
+
+
+def lowd_mpnn_backward(net: Mpnn):
+    net._check(load_library().lowd_mpnn_backward(net.ptr), "lowd_mpnn_backward")
+
+
+def lowd_mpnn_adam(net: Mpnn, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    net._check(load_library().lowd_mpnn_adam(net.ptr, float(lr), float(beta1), float(beta2), float(eps)),
+               "lowd_mpnn_adam")
+
+
+def lowd_mpnn_read(net: Mpnn, what: int) -> np.ndarray:
+    size = {LOWD_MPNN_SIGMA: net.m, LOWD_MPNN_LOADS: net.n, LOWD_MPNN_PHI: net.n,
+            LOWD_MPNN_FEATURES: 3 * net.n, LOWD_MPNN_GRAD: lowd_mpnn_param_count()}[what]
+    out = np.empty(max(size, 1), np.float32)
+    net._check(load_library().lowd_mpnn_read(net.ptr, int(what), _f32p(out), LOWD_MEM_HOST), "lowd_mpnn_read")
+    return out[:size]
+
+
+def lowd_warm_start(h: Handle, net: Mpnn):
+    """The network's splits on the handle's current graph become the LOWD state."""
+    h._check(load_library().lowd_warm_start(h.ptr, net.ptr), "lowd_warm_start")
+
+
+def lowd_mpnn_free(net: Mpnn):
+    if net is not None and net.ptr and net.ptr.value:
+        load_library().lowd_mpnn_free(net.ptr)
+        net.ptr = C.c_void_p(None)
