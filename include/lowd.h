@@ -371,6 +371,10 @@ lowd_status lowd_mpnn_get_params(lowd_mpnn net, float* params, int32_t mem);
 lowd_status lowd_mpnn_bind(lowd_mpnn net, int32_t n, int64_t m, const int32_t* lo, const int32_t* hi,
                            const float* w, const float* target, int32_t mem);
 
+/* Replace the bound graph's input features by caller-provided ones, x [3n] (node-major,
+ * three per node), host or device per mem; kept until the next bind. */
+lowd_status lowd_mpnn_set_features(lowd_mpnn net, const float* x, int32_t mem);
+
 /* Forward pass on the bound graph: splits sigma, their loads and, with a target, the loss
  * (loss may be NULL; a non-NULL loss without a target is LOWD_ERR_BAD_STATE). */
 lowd_status lowd_mpnn_forward(lowd_mpnn net, double* loss);

@@ -909,6 +909,16 @@ lowd_status lowd_mpnn_bind(lowd_mpnn c, int32_t n, int64_t m, const int32_t* lo,
                        mem == LOWD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
 }
 
+lowd_status lowd_mpnn_set_features(lowd_mpnn c, const float* x, int32_t mem) {
+    if (!c || !x || (mem != LOWD_MEM_HOST && mem != LOWD_MEM_DEVICE)) return LOWD_ERR_INVALID_ARG;
+    if (!c->bound) return LOWD_ERR_BAD_STATE;
+    const cudaMemcpyKind k = mem == LOWD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (c->n > 0) MP_CK(cudaMemcpyAsync(c->x, x, sizeof(float) * 3 * (size_t)c->n, k, c->st));
+    MP_CK(cudaStreamSynchronize(c->st));
+    c->forward_done = 0;
+    return LOWD_OK;
+}
+
 lowd_status lowd_mpnn_forward(lowd_mpnn c, double* loss) {
     if (!c) return LOWD_ERR_INVALID_ARG;
     if (!c->bound) return LOWD_ERR_BAD_STATE;

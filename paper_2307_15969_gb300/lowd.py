@@ -37,7 +37,7 @@ EXPORTED = (
     "lowd_batch_create", "lowd_batch_run", "lowd_batch_autotune", "lowd_batch_results",
     "lowd_batch_free", "lowd_batch_last_error", "lowd_batch_loads", "lowd_get_ldd",
     "lowd_ldd_dks_bound", "lowd_mpnn_param_count", "lowd_mpnn_create", "lowd_mpnn_set_params",
-    "lowd_mpnn_get_params", "lowd_mpnn_bind", "lowd_mpnn_forward", "lowd_mpnn_backward", "lowd_mpnn_adam",
+    "lowd_mpnn_get_params", "lowd_mpnn_bind", "lowd_mpnn_set_features", "lowd_mpnn_forward", "lowd_mpnn_backward", "lowd_mpnn_adam",
     "lowd_mpnn_read", "lowd_warm_start", "lowd_mpnn_last_error", "lowd_mpnn_free",
 )
 LOWD_MPNN_SIGMA = 1
@@ -115,6 +115,8 @@ def load_library(path: str = LIB_PATH):
     lib.lowd_mpnn_get_params.argtypes = [P, P, i32]
     lib.lowd_mpnn_bind.restype = i32
     lib.lowd_mpnn_bind.argtypes = [P, i32, C.c_int64, P, P, P, P, i32]
+    lib.lowd_mpnn_set_features.restype = i32
+    lib.lowd_mpnn_set_features.argtypes = [P, P, i32]
     lib.lowd_mpnn_forward.restype = i32
     lib.lowd_mpnn_forward.argtypes = [P, C.POINTER(C.c_double)]
     lib.lowd_mpnn_backward.restype = i32
@@ -537,6 +539,14 @@ def lowd_mpnn_bind(net: Mpnn, n: int, lo, hi, w=None, target=None):
                                       LOWD_MEM_HOST)
     net._check(s, "lowd_mpnn_bind")
     net.n, net.m = int(n), m
+
+
+def lowd_mpnn_set_features(net: Mpnn, x):
+    """Replace the bound graph's input features by x [n, 3]."""
+    xa = np.ascontiguousarray(x, np.float32).reshape(-1)
+    if xa.shape[0] != 3 * net.n:
+        raise ValueError("features must be [n, 3]")
+    net._check(load_library().lowd_mpnn_set_features(net.ptr, _f32p(xa), LOWD_MEM_HOST), "lowd_mpnn_set_features")
 
 
 def lowd_mpnn_forward(net: Mpnn, with_loss: bool = True):
