@@ -255,6 +255,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rho-max-passes", type=int, default=2000,
                     help="pass cap of the time-to-rho leg")
+    ap.add_argument("--no-warm-start", action="store_true", help="skip the warm-start time-to-rho leg")
+    ap.add_argument("--warm-params", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                          "paper_2307_15969_gb300", "warmstart_params.npy"))
     ap.add_argument("--batch-graphs", type=int, default=4096,
                     help="graphs of the batched workload (--workload batch)")
     args = ap.parse_args()
@@ -380,6 +383,31 @@ def main():
                        "includes": "prune + colouring + passes + FP64 checks with extraction"}
         pkg.lowd_free(h)
 
+        # the same with the learned warm start: the network's splits replace the equal split
+        # (features + three layers on the pruned core, inside the timed region)
+        time_to_rho_warm = None
+        if not args.no_warm_start and os.path.exists(args.warm_params):
+            from paper_2307_15969_gb300 import warmstart
+            net = pkg.lowd_mpnn_create()
+            pkg.lowd_mpnn_set_params(net, warmstart.load_params(args.warm_params))
+            h = pkg.lowd_load_graph(g.n, du, dv, dw, stream=stream)
+            t_a.record(stream)
+            pkg.lowd_prune(h)
+            t_w = torch.cuda.Event(enable_timing=True)
+            pkg.lowd_warm_start(h, net)
+            t_w.record(stream)
+            st_w = pkg.lowd_iterate(h, args.rho_max_passes, check_every=check, rel_tol=1e-6)
+            t_b.record(stream)
+            t_b.synchronize()
+            time_to_rho_warm = {"rel_gap": 1e-6, "converged": bool(st_w["converged"]),
+                                "passes": int(st_w["iters_done"]), "ms": t_a.elapsed_time(t_b),
+                                "warm_start_ms": t_a.elapsed_time(t_w),
+                                "check_every": check, "rho": st_w["rho_best"], "D": st_w["max_load"],
+                                "params": os.path.basename(args.warm_params),
+                                "includes": "prune + network inference + colouring + passes + FP64 checks"}
+            pkg.lowd_free(h)
+            pkg.lowd_mpnn_free(net)
+
         # end to end through the C ABI with pinned host buffers (copies inside the timing)
         hu = torch.from_numpy(g.u).pin_memory().numpy()
         hv = torch.from_numpy(g.v).pin_memory().numpy()
@@ -424,6 +452,7 @@ def main():
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
         "stages_ms": stages,
         "time_to_rho": time_to_rho,
+        "time_to_rho_warm_start": time_to_rho_warm,
         "gpu_launches": int(launches),
         "gpu_launches_per_step": int(launches // max(args.steps, 1)),
         "clocks": ck,

@@ -327,6 +327,11 @@ lowd_status lowd_batch_results(lowd_batch b, double* rho, int32_t* S_size, uint8
  * circle colouring of the core, ids renumbered ascending) in ascending colour. */
 lowd_status lowd_batch_loads(lowd_batch b, float* loads);
 
+/* Core membership after the last run, by local id, host or device per `mem`: in_core
+ * [node_off[B]] = 1 if the node survived Algorithm 2 (0 as well for graphs with a nonzero
+ * status).  With lowd_batch_loads this gives each graph's pruned core and its loads. */
+lowd_status lowd_batch_core(lowd_batch b, uint8_t* in_core);
+
 /* Text of the last CUDA error seen by this batch ("" if none). */
 const char* lowd_batch_last_error(lowd_batch b);
 

@@ -57,6 +57,7 @@ struct BatchArgs {
     int32_t* status;           // [B]
     uint8_t* in_S;             // [n_total]
     float* loads;              // [n_total] loads after the passes (0 for pruned nodes)
+    uint8_t* in_core;          // [n_total] 1 if the node survived Algorithm 2
 };
 
 __device__ __forceinline__ int32_t block_sum_i32(int32_t x, int32_t* red) {
@@ -127,7 +128,8 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
         int32_t* oldid = A.oldid + n0;
         uint8_t* inS = A.in_S + n0;
         float* lout = A.loads + n0;
-        for (int32_t i = tid; i < n; i += nt) { inS[i] = 0; lout[i] = 0.0f; }
+        uint8_t* cout = A.in_core + n0;
+        for (int32_t i = tid; i < n; i += nt) { inS[i] = 0; lout[i] = 0.0f; cout[i] = 0; }
         if ((uint64_t)n * 5u + 64u > A.smem_bytes || n > 65535) {
             if (tid == 0) { A.status[g] = BS_TOO_MANY_NODES; A.rho[g] = 0.0; A.S_size[g] = 0; }
             continue;
@@ -426,7 +428,10 @@ __global__ void __launch_bounds__(1024, 1) k_batch_lowd(BatchArgs A) {
                 }
             }
         }
-        for (int32_t i = tid; i < nH; i += nt) lout[oldid[i]] = L[i];
+        for (int32_t i = tid; i < nH; i += nt) {
+            lout[oldid[i]] = L[i];
+            cout[oldid[i]] = 1;
+        }
         // ---------------- extraction
         unsigned long long* keys = reinterpret_cast<unsigned long long*>(cursor + P + 1);  // [npow]
         keys = reinterpret_cast<unsigned long long*>(((uintptr_t)keys + 7) & ~(uintptr_t)7);
@@ -545,6 +550,7 @@ struct lowd_batch_ctx {
     int32_t *S_size = nullptr, *nH = nullptr, *mH = nullptr, *rounds = nullptr, *status = nullptr;
     uint8_t* in_S = nullptr;
     float* loads = nullptr;
+    uint8_t* in_core = nullptr;
     // tuned launch
     lowd_batch_options tuned{};
     int have_tuned = 0;
@@ -574,7 +580,7 @@ void batch_free_all(lowd_batch_ctx* b) {
     if (b->own_stream && b->st) cudaStreamDestroy(b->st);
     b->st = nullptr;
     void* ps[] = {b->node_off, b->edge_off, b->u, b->v, b->eA, b->eB, b->cs, b->oldid, b->order, b->queue,
-                  b->rho, b->S_size, b->nH, b->mH, b->rounds, b->status, b->in_S, b->loads};
+                  b->rho, b->S_size, b->nH, b->mH, b->rounds, b->status, b->in_S, b->loads, b->in_core};
     for (void* p : ps)
         if (p) cudaFree(p);
 }
@@ -638,7 +644,7 @@ cudaError_t enqueue(lowd_batch_ctx* b, const lowd_batch_options& o, int32_t coun
     A.eA = b->eA; A.eB = b->eB; A.cs = b->cs; A.oldid = b->oldid; A.order = b->order; A.queue = b->queue;
     A.passes = o.passes; A.smem_bytes = (uint32_t)cfg.smem;
     A.rho = b->rho; A.S_size = b->S_size; A.nH = b->nH; A.mH = b->mH; A.rounds = b->rounds;
-    A.status = b->status; A.in_S = b->in_S; A.loads = b->loads;
+    A.status = b->status; A.in_S = b->in_S; A.loads = b->loads; A.in_core = b->in_core;
     cudaError_t e = cudaMemsetAsync(b->queue, 0, sizeof(int32_t), b->st);
     if (e != cudaSuccess) return e;
     LOWD_LAUNCH(k_batch_lowd, cfg.grid, cfg.threads, cfg.smem, b->st, A);
@@ -710,6 +716,7 @@ lowd_status lowd_batch_create(int32_t B, const int64_t* node_off, const int64_t*
         if (a == cudaSuccess) a = balloc(&b->status, (size_t)B);
         if (a == cudaSuccess) a = balloc(&b->in_S, n);
         if (a == cudaSuccess) a = balloc(&b->loads, n);
+        if (a == cudaSuccess) a = balloc(&b->in_core, n);
         if (a != cudaSuccess) s = b->fail(a);
     }
     if (s == LOWD_OK) {
@@ -855,6 +862,15 @@ lowd_status lowd_batch_loads(lowd_batch b, float* loads) {
     if (!b || !loads) return LOWD_ERR_INVALID_ARG;
     const cudaMemcpyKind k = b->mem == LOWD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     cudaError_t e = cudaMemcpyAsync(loads, b->loads, sizeof(float) * (size_t)b->n_total, k, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return b->fail(e);
+    return LOWD_OK;
+}
+
+lowd_status lowd_batch_core(lowd_batch b, uint8_t* in_core) {
+    if (!b || !in_core) return LOWD_ERR_INVALID_ARG;
+    const cudaMemcpyKind k = b->mem == LOWD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpyAsync(in_core, b->in_core, (size_t)b->n_total, k, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return b->fail(e);
     return LOWD_OK;

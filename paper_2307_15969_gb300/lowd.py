@@ -35,7 +35,7 @@ EXPORTED = (
     "lowd_get_prune_info", "lowd_get_edge_order", "lowd_free", "lowd_status_string",
     "lowd_last_error", "lowd_launch_count", "lowd_extract_noalloc",
     "lowd_batch_create", "lowd_batch_run", "lowd_batch_autotune", "lowd_batch_results",
-    "lowd_batch_free", "lowd_batch_last_error", "lowd_batch_loads", "lowd_get_ldd",
+    "lowd_batch_free", "lowd_batch_last_error", "lowd_batch_loads", "lowd_batch_core", "lowd_get_ldd",
     "lowd_ldd_dks_bound", "lowd_mpnn_param_count", "lowd_mpnn_create", "lowd_mpnn_set_params",
     "lowd_mpnn_get_params", "lowd_mpnn_bind", "lowd_mpnn_set_features", "lowd_mpnn_forward", "lowd_mpnn_backward", "lowd_mpnn_adam",
     "lowd_mpnn_read", "lowd_warm_start", "lowd_mpnn_last_error", "lowd_mpnn_free",
@@ -161,6 +161,8 @@ def load_library(path: str = LIB_PATH):
     lib.lowd_batch_autotune.argtypes = [P, i32, i32, C.POINTER(lowd_batch_options)]
     lib.lowd_batch_results.restype = i32
     lib.lowd_batch_results.argtypes = [P, P, P, P, P, P, P, P]
+    lib.lowd_batch_core.restype = i32
+    lib.lowd_batch_core.argtypes = [P, P]
     lib.lowd_batch_loads.restype = i32
     lib.lowd_batch_loads.argtypes = [P, P]
     lib.lowd_batch_last_error.restype = C.c_char_p
@@ -465,6 +467,15 @@ def lowd_batch_loads(b: Batch) -> np.ndarray:
     s = load_library().lowd_batch_loads(b.ptr, out.ctypes.data_as(C.c_void_p))
     if s != LOWD_OK:
         raise LowdError(s, "lowd_batch_loads", load_library().lowd_batch_last_error(b.ptr).decode())
+    return out[:b.n_total]
+
+
+def lowd_batch_core(b: Batch) -> np.ndarray:
+    """1 for nodes that survived Algorithm 2 in the last run, all graphs by local id."""
+    out = np.empty(max(b.n_total, 1), np.uint8)
+    s = load_library().lowd_batch_core(b.ptr, out.ctypes.data_as(C.c_void_p))
+    if s != LOWD_OK:
+        raise LowdError(s, "lowd_batch_core", load_library().lowd_batch_last_error(b.ptr).decode())
     return out[:b.n_total]
 
 

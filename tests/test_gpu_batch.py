@@ -80,6 +80,7 @@ def test_batch_same_order_loads(setup, T):
         pkg.lowd_batch_run(b, passes=T, threads=thr)
         res = pkg.lowd_batch_results(b)
         lg = pkg.lowd_batch_loads(b)
+        core = pkg.lowd_batch_core(b)
         for i, g in enumerate(graphs):
             assert res["status"][i] == 0, i
             nh, uh, vh, _, idmap = oracle_graph(orc, g, True)
@@ -88,6 +89,7 @@ def test_batch_same_order_loads(setup, T):
             o.iterate(T, order=order)
             li = lg[node_off[i]:node_off[i + 1]].astype(np.float64)
             assert np.all(li[~ref[i]["keep"]] == 0), i
+            assert np.array_equal(core[node_off[i]:node_off[i + 1]].astype(bool), ref[i]["keep"]), i
             err = np.max(np.abs(li[idmap] - o.l)) if nh else 0.0
             assert err <= 1e-4 * max(1.0, o.l.max() if nh else 1.0), (i, T, thr, err)
     pkg.lowd_batch_free(b)

@@ -184,7 +184,10 @@ def test_random_parameters_within_the_bf16_footprint(pkg, n, m, seed, weighted):
     ld = pkg.lowd_mpnn_read(net, pkg.LOWD_MPNN_LOADS)
     d, e = np.abs(ld - ref["loads"]), np.abs(ref["loads"] - r64["loads"])
     assert d.max() <= 2 * e.max() + 1e-5 * ref["loads"].max() and np.median(d) <= np.median(e) + 1e-6 * ref["loads"].max()
-    assert abs(loss - ref["loss"]) <= 2 * abs(ref["loss"] - r64["loss"]) + 1e-5 * ref["loss"]
+    # the scalar loss sums signed rounding effects that cancel, so its own footprint is no
+    # bound: check it against the GPU's loads (the reduction is pinned on the exact grid)
+    ld64 = ld.astype(np.float64)
+    assert abs(loss - np.sum((ld64 - t) ** 2) / np.sum(t * t)) <= 1e-5 * loss
     pkg.lowd_mpnn_backward(net)
     g = pkg.lowd_mpnn_read(net, pkg.LOWD_MPNN_GRAD).astype(np.float64)
     gr, g64 = omp.backward(p, ref), omp.backward(p, r64)
