@@ -27,7 +27,7 @@ void free_all(lowd_ctx* h) {
     dfree(&h->u); dfree(&h->v); dfree(&h->w); dfree(&h->wu); dfree(&h->map);
     dfree(&h->sort_perm); dfree(&h->removal_round);
     dfree(&h->perm); dfree(&h->coff); dfree(&h->coff_real); dfree(&h->cuv);
-    dfree(&h->cw); dfree(&h->cs); dfree(&h->l);
+    dfree(&h->cw); dfree(&h->cs); dfree(&h->l); dfree(&h->l_lo);
     dfree(&h->tmp); h->tmp_cap = 0;
     dfree(&h->d_stats); dfree(&h->d_i64); dfree(&h->d_i32);
     if (h->h_pin) cudaFreeHost(h->h_pin);

@@ -59,6 +59,7 @@ struct lowd_ctx {
     float* cw = nullptr;       // [m_pad] weights (weighted only); padding 0
     float* cs = nullptr;       // [m_pad] splits f_e(lo); padding 0
     float* l = nullptr;        // [n + 1] loads; slot n is the padding sentinel
+    float* l_lo = nullptr;     // [n + 1] low parts: the load is l + l_lo (pair arithmetic in the sweep)
 
     // scratch
     void* tmp = nullptr;

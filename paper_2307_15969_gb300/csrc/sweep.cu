@@ -152,15 +152,19 @@ __global__ void k_rederive(int64_t m_pad, const uint32_t* __restrict__ cuv, cons
     }
 }
 
-// l = (float) L64; stats[0] += sum l, stats[1] += sum l^2, stats[2] = max l (FP64)
+// (l, l_lo) = L64 as an FP32 pair; stats[0] += sum l, stats[1] += sum l^2, stats[2] = max l (FP64)
 __global__ void k_load_stats(const double* __restrict__ L64, int32_t n, float* __restrict__ l,
-                             double* __restrict__ stats) {
+                             float* __restrict__ l_lo, double* __restrict__ stats) {
     __shared__ double sh[kT / 32 + 1];
     double s1 = 0.0, s2 = 0.0, mx = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double x = L64[i];
-        if (l) l[i] = (float)x;
+        if (l) {
+            const float hi = (float)x;
+            l[i] = hi;
+            l_lo[i] = (float)(x - (double)hi);   // the pair (hi, lo) carries x to ~2^-48
+        }
         s1 += x; s2 += x * x; mx = fmax(mx, x);
     }
     double t1 = block_sum(s1, sh);
@@ -226,6 +230,37 @@ __device__ __forceinline__ float lowd_transfer(EdgeVal& e) {
     e.la -= dd;
     e.lb += dd;
     return fminf(e.s - dd, e.w);
+}
+
+// Loads as unevaluated FP32 pairs hi + lo (|lo| <= ulp(hi) / 2).  A transfer moves d with
+// Knuth's error-free TwoSum, so no update rounds a load: a node with thousands of updates a
+// pass would otherwise carry a rounding walk of several ulp(l) per pass, which is what
+// limits the reachable duality gap in plain FP32 (about 1e-6 relative at loads near 700).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+    s = a + b;
+    const float bb = s - a;
+    err = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void comp_add(float2& x, float v) {
+    float t, e;
+    two_sum(x.x, v, t, e);
+    const float lo = x.y + e;
+    const float u = t + lo;        // renormalise: hi = fl(t + lo), lo = exact remainder
+    x.y = lo - (u - t);
+    x.x = u;
+}
+
+// Algorithm 1's edge update on pair loads: returns the new split f_e(lo).
+__device__ __forceinline__ float comp_transfer(float2& A, float2& B, float s, float w) {
+    const float diff = (A.x - B.x) + (A.y - B.y);
+    const bool gt = diff > 0.0f;
+    const float cap = gt ? s : (w - s);
+    const float d = fminf(fabsf(diff) * 0.5f, cap);
+    const float dd = gt ? d : -d;
+    comp_add(A, -dd);
+    comp_add(B, dd);
+    return fminf(s - dd, w);
 }
 
 __device__ __forceinline__ uint32_t end_a(uint32_t uv) { return uv & 0xffffu; }
@@ -297,12 +332,13 @@ template <bool WEIGHTED, int kRing, bool CO_SMEM>
 __global__ void __launch_bounds__(kVecThreads, 1)
 k_sweep_vec(int32_t n, int32_t C, const int32_t* __restrict__ coff,
             const uint4* __restrict__ cuv, const float4* __restrict__ cw, float4* __restrict__ cs,
-            float* __restrict__ l, int32_t passes) {
+            float* __restrict__ l, float* __restrict__ l_lo, int32_t passes) {
     extern __shared__ float L[];
     int32_t* COs = reinterpret_cast<int32_t*>(L + n + 1);
     const int tid = threadIdx.x;
     const int B = blockDim.x;
-    for (int i = tid; i <= n; i += B) L[i] = i < n ? l[i] : 0.0f;
+    // plain FP32 loads here: a pair load's low part is folded in and cleared on exit
+    for (int i = tid; i <= n; i += B) L[i] = i < n ? l[i] + l_lo[i] : 0.0f;
     if (CO_SMEM)
         for (int i = tid; i <= C; i += B) COs[i] = coff[i];
     __syncthreads();
@@ -334,7 +370,10 @@ k_sweep_vec(int32_t n, int32_t C, const int32_t* __restrict__ coff,
             }
         }
     }
-    for (int i = tid; i < n; i += B) l[i] = L[i];
+    for (int i = tid; i < n; i += B) {
+        l[i] = L[i];
+        l_lo[i] = 0.0f;
+    }
 }
 
 // ------------------------------------------------------------------ bulk-copy staged sweep
@@ -370,7 +409,7 @@ __host__ __device__ inline TmaLayout tma_layout(int32_t n, int32_t C, int32_t S,
     TmaLayout t;
     t.bars = 0;
     t.L = 16u * kTmaMaxStages;   // S full + S empty mbarriers
-    t.CO = t.L + 4u * (uint32_t)(n + 1);
+    t.CO = t.L + 8u * (uint32_t)(n + 1);   // loads as (hi, lo) pairs
     uint32_t end = t.CO + 4u * (uint32_t)(C + 1);
     t.stages = (end + 127u) & ~127u;
     t.arr_bytes = ((4u * (uint32_t)Emax) + 127u) & ~127u;
@@ -382,19 +421,20 @@ __host__ __device__ inline TmaLayout tma_layout(int32_t n, int32_t C, int32_t S,
 template <bool WEIGHTED, int E>
 __global__ void __launch_bounds__(kTmaConsumers + 32, 1)
 k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32_t* __restrict__ cuv,
-            const float* __restrict__ cw, float* __restrict__ cs, float* __restrict__ l, int32_t passes,
-            int32_t S, int32_t G, int32_t Emax, int32_t* __restrict__ err) {
+            const float* __restrict__ cw, float* __restrict__ cs, float* __restrict__ l,
+            float* __restrict__ l_lo, int32_t passes, int32_t S, int32_t G, int32_t Emax,
+            int32_t* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     const TmaLayout lay = tma_layout(n, C, S, Emax, WEIGHTED);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bars);
     uint64_t* empty = full + S;   // S full barriers, then S empty barriers
-    float* L = reinterpret_cast<float*>(smem + lay.L);
+    float2* L = reinterpret_cast<float2*>(smem + lay.L);   // (hi, lo) per node; slot n: padding
     int32_t* CO = reinterpret_cast<int32_t*>(smem + lay.CO);
     unsigned char* stages = smem + lay.stages;
     __shared__ volatile int32_t abort_flag;
     const int tid = threadIdx.x;
     const int nc = blockDim.x - 32;          // consumer threads; the last warp produces
-    for (int i = tid; i <= n; i += blockDim.x) L[i] = i < n ? l[i] : 0.0f;
+    for (int i = tid; i <= n; i += blockDim.x) L[i] = i < n ? make_float2(l[i], l_lo[i]) : make_float2(0.0f, 0.0f);
     for (int i = tid; i <= C; i += blockDim.x) CO[i] = coff[i];
     if (tid == 0) {
         abort_flag = 0;
@@ -493,20 +533,21 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
                     e[jj].s = r < ce ? ss[r] : 0.0f;
                     e[jj].w = WEIGHTED ? (r < ce ? sw[r] : 0.0f) : 1.0f;
                 }
+                float2 A[E], Bv[E];
 #pragma unroll
                 for (int jj = 0; jj < E; ++jj) {
-                    e[jj].la = L[end_a(uv[jj])];
-                    e[jj].lb = L[end_b(uv[jj])];
+                    A[jj] = L[end_a(uv[jj])];
+                    Bv[jj] = L[end_b(uv[jj])];
                 }
                 float ns[E];
 #pragma unroll
-                for (int jj = 0; jj < E; ++jj) ns[jj] = lowd_transfer(e[jj]);
+                for (int jj = 0; jj < E; ++jj) ns[jj] = comp_transfer(A[jj], Bv[jj], e[jj].s, e[jj].w);
 #pragma unroll
                 for (int jj = 0; jj < E; ++jj) {
                     const int32_t r = r0 + jj * nc;
                     if (r < ce) {
-                        L[end_a(uv[jj])] = e[jj].la;
-                        L[end_b(uv[jj])] = e[jj].lb;
+                        L[end_a(uv[jj])] = A[jj];
+                        L[end_b(uv[jj])] = Bv[jj];
                         ss[r] = ns[jj];
                     }
                 }
@@ -527,7 +568,10 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         abort_flag = 1;
         atomicOr(err, 1);
     }
-    for (int i = tid; i < n; i += nc) l[i] = L[i];
+    for (int i = tid; i < n; i += nc) {
+        l[i] = L[i].x;
+        l_lo[i] = L[i].y;
+    }
 }
 
 // Schedules with fewer classes than the ring depth: same layout, no prefetch ring.
@@ -535,11 +579,12 @@ template <bool WEIGHTED>
 __global__ void __launch_bounds__(kVecThreads, 1)
 k_sweep_simple(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint4* __restrict__ cuv,
                const float4* __restrict__ cw, float4* __restrict__ cs, float* __restrict__ l,
-               int32_t passes) {
+               float* __restrict__ l_lo, int32_t passes) {
     extern __shared__ float L[];
     const int tid = threadIdx.x;
     const int B = blockDim.x;
-    for (int i = tid; i <= n; i += B) L[i] = i < n ? l[i] : 0.0f;
+    // plain FP32 loads here: a pair load's low part is folded in and cleared on exit
+    for (int i = tid; i <= n; i += B) L[i] = i < n ? l[i] + l_lo[i] : 0.0f;
     __syncthreads();
     for (int32_t t = 0; t < passes; ++t)
         for (int32_t c = 0; c < C; ++c) {
@@ -551,7 +596,10 @@ k_sweep_simple(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uin
             }
             __syncthreads();
         }
-    for (int i = tid; i < n; i += B) l[i] = L[i];
+    for (int i = tid; i < n; i += B) {
+        l[i] = L[i];
+        l_lo[i] = 0.0f;
+    }
 }
 
 template <bool WEIGHTED>
@@ -588,8 +636,8 @@ cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* 
     const int32_t per = (int32_t)(0x7fffffff / NC);
     for (int32_t done = 0; done < passes && e == cudaSuccess;) {
         const int32_t k = passes - done < per ? passes - done : per;
-        LOWD_LAUNCH(kern, 1, threads + 32, lay.total, h->st, h->n, h->C, h->coff, h->cuv, h->cw, h->cs, h->l, k,
-                    S, G, chunk, h->d_i32 + 8);
+        LOWD_LAUNCH(kern, 1, threads + 32, lay.total, h->st, h->n, h->C, h->coff, h->cuv, h->cw, h->cs, h->l,
+                    h->l_lo, k, S, G, chunk, h->d_i32 + 8);
         e = cudaGetLastError();
         done += k;
     }
@@ -624,12 +672,12 @@ cudaError_t launch_sweep(lowd_ctx* h, int32_t passes) {
         auto kern = co_smem ? k_sweep_vec<WEIGHTED, kRing, true> : k_sweep_vec<WEIGHTED, kRing, false>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        LOWD_LAUNCH(kern, 1, threads, smem, h->st, h->n, h->C, h->coff, cuv, cw, cs, h->l, passes);
+        LOWD_LAUNCH(kern, 1, threads, smem, h->st, h->n, h->C, h->coff, cuv, cw, cs, h->l, h->l_lo, passes);
     } else {
         auto kern = k_sweep_simple<WEIGHTED>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lbytes);
         if (e != cudaSuccess) return e;
-        LOWD_LAUNCH(kern, 1, threads, lbytes, h->st, h->n, h->C, h->coff, cuv, cw, cs, h->l, passes);
+        LOWD_LAUNCH(kern, 1, threads, lbytes, h->st, h->n, h->C, h->coff, cuv, cw, cs, h->l, h->l_lo, passes);
     }
     return cudaGetLastError();
 }
@@ -725,6 +773,7 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
         if (h->w && (s = dalloc(h, &h->cw, m_pad))) break;
         if ((s = dalloc(h, &h->cs, m_pad))) break;
         if ((s = dalloc(h, &h->l, (size_t)n + 1))) break;
+        if ((s = dalloc(h, &h->l_lo, (size_t)n + 1))) break;
         if (m_pad > 0)
             LOWD_LAUNCH(k_gather_streams, grid_for(m_pad), kT, 0, st, h->perm, m_pad, n, h->u, h->v, h->w,
                         init_splits_canon, h->cuv, h->cw, h->cs);
@@ -746,7 +795,7 @@ lowd_status lowd_sweep_rederive(lowd_ctx* h, double* stats3) {
     cudaMemsetAsync(L64, 0, sizeof(double) * (size_t)h->n, st);
     cudaMemsetAsync(h->d_stats, 0, 3 * sizeof(double), st);
     if (h->m_pad > 0) LOWD_LAUNCH(k_rederive, grid_for(h->m_pad), kT, 0, st, h->m_pad, h->cuv, h->cw, h->cs, L64);
-    LOWD_LAUNCH(k_load_stats, grid_for(h->n), kT, 0, st, L64, h->n, h->l, h->d_stats);
+    LOWD_LAUNCH(k_load_stats, grid_for(h->n), kT, 0, st, L64, h->n, h->l, h->l_lo, h->d_stats);
     double tmp3[3];
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(tmp3, h->d_stats, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
