@@ -405,12 +405,17 @@ struct TmaLayout {
     uint32_t bars, L, CO, stages, stage_bytes, arr_bytes, total;
 };
 
-__host__ __device__ inline TmaLayout tma_layout(int32_t n, int32_t C, int32_t S, int32_t Emax, bool weighted) {
+// Shared memory: mbarriers, loads as (hi, lo) pairs, the chunk boundaries (offsets of
+// classes 0, G, 2G, ..., C), then the stages.  Offsets of the classes inside a chunk are not
+// kept here: each consumer warp holds them in a register, fetched one chunk ahead.
+__host__ __device__ inline TmaLayout tma_layout(int32_t n, int32_t C, int32_t S, int32_t Emax, bool weighted,
+                                                int32_t G) {
     TmaLayout t;
     t.bars = 0;
     t.L = 16u * kTmaMaxStages;   // S full + S empty mbarriers
-    t.CO = t.L + 8u * (uint32_t)(n + 1);   // loads as (hi, lo) pairs
-    uint32_t end = t.CO + 4u * (uint32_t)(C + 1);
+    t.CO = t.L + 8u * (uint32_t)(n + 1);
+    const uint32_t NC = (uint32_t)((C + G - 1) / G);
+    uint32_t end = t.CO + 4u * (NC + 1u);
     t.stages = (end + 127u) & ~127u;
     t.arr_bytes = ((4u * (uint32_t)Emax) + 127u) & ~127u;
     t.stage_bytes = t.arr_bytes * (weighted ? 3u : 2u);
@@ -425,17 +430,18 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
             float* __restrict__ l_lo, int32_t passes, int32_t S, int32_t G, int32_t Emax,
             int32_t* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const TmaLayout lay = tma_layout(n, C, S, Emax, WEIGHTED);
+    const TmaLayout lay = tma_layout(n, C, S, Emax, WEIGHTED, G);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bars);
     uint64_t* empty = full + S;   // S full barriers, then S empty barriers
     float2* L = reinterpret_cast<float2*>(smem + lay.L);   // (hi, lo) per node; slot n: padding
-    int32_t* CO = reinterpret_cast<int32_t*>(smem + lay.CO);
+    int32_t* CK = reinterpret_cast<int32_t*>(smem + lay.CO);   // CK[j] = offset of class j G
     unsigned char* stages = smem + lay.stages;
     __shared__ volatile int32_t abort_flag;
     const int tid = threadIdx.x;
     const int nc = blockDim.x - 32;          // consumer threads; the last warp produces
+    const int32_t NC = (C + G - 1) / G;      // chunks of G classes per pass
     for (int i = tid; i <= n; i += blockDim.x) L[i] = i < n ? make_float2(l[i], l_lo[i]) : make_float2(0.0f, 0.0f);
-    for (int i = tid; i <= C; i += blockDim.x) CO[i] = coff[i];
+    for (int i = tid; i <= NC; i += blockDim.x) CK[i] = coff[min(i * G, C)];
     if (tid == 0) {
         abort_flag = 0;
         for (int k = 0; k < S; ++k) {
@@ -446,7 +452,6 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         fence_proxy_async_smem();
     }
     __syncthreads();
-    const int32_t NC = (C + G - 1) / G;      // chunks of G classes per pass
     const int32_t P = NC * passes;           // the launcher keeps this < 2^31
     const int32_t ahead = S - kStoreSlack;   // chunks loaded ahead of the consumers
     if (tid >= nc) {
@@ -454,8 +459,8 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         if (tid == nc) {
             int32_t pf = 0, kf = 0, jf = 0;  // next fill: stream position, stage, chunk
             auto fill = [&]() {
-                const int32_t beg = CO[jf * G];
-                const int32_t end = CO[min(jf * G + G, C)];
+                const int32_t beg = CK[jf];
+                const int32_t end = CK[jf + 1];
                 const uint32_t bytes = 4u * (uint32_t)(end - beg);
                 unsigned char* st = stages + lay.stage_bytes * (uint32_t)kf;
                 mbar_expect_tx(&full[kf], bytes * (WEIGHTED ? 3u : 2u));
@@ -475,8 +480,8 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
                 bool ok = mbar_try_wait_sleep(&empty[k], parity, 1000);
                 while (!ok && !abort_flag && ++spins < kWaitLimit) ok = mbar_try_wait_sleep(&empty[k], parity, 1000);
                 if (!ok) { abort_flag = 1; break; }
-                const int32_t beg = CO[j * G];
-                const int32_t end = CO[min(j * G + G, C)];
+                const int32_t beg = CK[j];
+                const int32_t end = CK[j + 1];
                 bulk_s2g(cs + beg, stages + lay.stage_bytes * (uint32_t)k + lay.arr_bytes, 4u * (uint32_t)(end - beg));
                 bulk_commit();
                 if (pf < P) {
@@ -507,6 +512,14 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         while (!ok && ++spins < kWaitLimit) ok = mbar_try_wait(&full[kk], par);
         return ok;
     };
+    // lane i of every consumer warp holds the offset of class jc G + i (i <= G) of a chunk
+    const int lane = tid & 31;
+    auto class_offsets = [&](int32_t jc) -> int32_t {
+        const int32_t c = jc * G + lane;
+        return (lane <= G && c <= C) ? __ldg(coff + c) : 0;
+    };
+    int32_t off_cur = class_offsets(0);
+    int32_t off_nxt = class_offsets(NC > 1 ? 1 : 0);
     bool bad = false;
     if (tid < 32 && P > 0) bad = !wait_full(0, 0);
     bad = consumer_sync_or(nc, bad);
@@ -515,14 +528,14 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
     for (int32_t q = 0; q < P && !bad; ++q) {
         const int32_t c0 = j * G;
         const int32_t c1 = min(c0 + G, C);
-        const int32_t base = CO[c0];
+        const int32_t base = __shfl_sync(0xffffffffu, off_cur, 0);
         unsigned char* st = stages + lay.stage_bytes * (uint32_t)k;
         const uint32_t* suv = reinterpret_cast<const uint32_t*>(st);
         float* ss = reinterpret_cast<float*>(st + lay.arr_bytes);
         const float* sw = reinterpret_cast<const float*>(st + 2 * lay.arr_bytes);
         int32_t cb = 0;
         for (int32_t c = c0; c < c1; ++c) {
-            const int32_t ce = CO[c + 1] - base;
+            const int32_t ce = __shfl_sync(0xffffffffu, off_cur, c - c0 + 1) - base;
             for (int32_t r0 = cb + tid; r0 < ce; r0 += E * nc) {
                 uint32_t uv[E];
                 EdgeVal e[E];
@@ -559,6 +572,8 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         const int32_t kprev = k;
         if (++k == S) { k = 0; parity ^= 1u; }
         j = (j + 1 == NC) ? 0 : j + 1;
+        off_cur = off_nxt;                                   // chunk j's offsets, fetched a chunk ago
+        off_nxt = class_offsets(j + 1 == NC ? 0 : j + 1);
         bool fail = false;
         if (tid < 32 && q + 1 < P) fail = !wait_full(k, parity);
         bad = consumer_sync_or(nc, fail);
@@ -615,8 +630,8 @@ cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* 
         int32_t mx = 0;  // longest chunk of g classes
         for (int32_t c0 = 0; c0 < h->C; c0 += g) mx = max(mx, h->coff_h[min(c0 + g, h->C)] - h->coff_h[c0]);
         int32_t s = kTmaMaxStages;
-        TmaLayout t = tma_layout(h->n, h->C, s, mx, WEIGHTED);
-        while (s > kMinStages && t.total > budget) t = tma_layout(h->n, h->C, --s, mx, WEIGHTED);
+        TmaLayout t = tma_layout(h->n, h->C, s, mx, WEIGHTED, g);
+        while (s > kMinStages && t.total > budget) t = tma_layout(h->n, h->C, --s, mx, WEIGHTED, g);
         if (t.total <= budget) { G = g; S = s; chunk = mx; lay = t; break; }
     }
     if (G == 0) return cudaSuccess;
