@@ -242,13 +242,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) 
     err = (a - (s - bb)) + (b - bb);
 }
 
+// x.x + x.y += v: the rounding error of the high sum goes to the low part.  The low part is
+// not renormalised per update: it gathers a random walk of errors of at most ulp(hi) / 2
+// each (about sqrt(updates) ulp(hi), still far below hi), and the kernel renormalises once
+// when it writes the loads back.
 __device__ __forceinline__ void comp_add(float2& x, float v) {
     float t, e;
     two_sum(x.x, v, t, e);
-    const float lo = x.y + e;
-    const float u = t + lo;        // renormalise: hi = fl(t + lo), lo = exact remainder
-    x.y = lo - (u - t);
-    x.x = u;
+    x.x = t;
+    x.y += e;
 }
 
 // Algorithm 1's edge update on pair loads: returns the new split f_e(lo).
@@ -584,8 +586,10 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         atomicOr(err, 1);
     }
     for (int i = tid; i < n; i += nc) {
-        l[i] = L[i].x;
-        l_lo[i] = L[i].y;
+        const float2 x = L[i];
+        const float u = x.x + x.y;     // renormalise: l = fl(hi + lo), l_lo = exact remainder
+        l[i] = u;
+        l_lo[i] = x.y - (u - x.x);
     }
 }
 
