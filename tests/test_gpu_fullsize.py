@@ -68,11 +68,20 @@ def test_rmat22_prune_core_and_passes(setup):
     s = pkg.lowd_get_splits(h).cpu().numpy()
     assert np.all(s >= 0) and np.all(s <= 1)
 
-    # extraction: bit-exact against the oracle on the GPU's loads; weak duality
+    # weak duality on the GPU's own state
     S, rho, _ = pkg.lowd_extract(h, want_loads=False)
-    So, Wo = orc.extract(nh, uh, vh, np.ones(uh.shape[0], np.int64), lg)
+    assert rho <= st2["max_load"] * (1 + 1e-12)
+    # extraction bit-exact from the oracle's state: its splits become the handle's, both
+    # sides extract from the FP32 rounding of the FP64 loads those splits imply
+    import torch
+    s32 = o.fu.astype(np.float32)
+    pkg.lowd_set_splits(h, torch.from_numpy(s32).cuda())
+    S, rho, _ = pkg.lowd_extract(h, want_loads=False)
+    l64 = np.zeros(nh)
+    np.add.at(l64, uh, s32.astype(np.float64))
+    np.add.at(l64, vh, 1.0 - s32.astype(np.float64))
+    So, Wo = orc.extract(nh, uh, vh, np.ones(uh.shape[0], np.int64), l64.astype(np.float32).astype(np.float64))
     idmap = np.nonzero(keep)[0]
     assert np.array_equal(S.cpu().numpy(), idmap[So])
     assert rho == Wo / So.shape[0]
-    assert rho <= st2["max_load"] * (1 + 1e-12)
     pkg.lowd_free(h)

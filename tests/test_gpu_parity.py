@@ -3,8 +3,8 @@
 Bars (bit-exact where the work is integer, tolerance where it is floating point):
  - canonical edge list, counting-sort order, pruning rounds and the pruned graph H:
    bit-exact;
- - extraction: the GPU's S* and W(S*) equal the oracle's extraction run on the same FP32
-   loads (the order decision is taken in FP32 on both sides), bit-exact;
+ - extraction: from the oracle's own state (its splits set on the GPU handle), the GPU's S*
+   and W(S*) equal the oracle's extraction on the same FP32 loads, bit-exact;
  - same-order LOWD: the GPU's classes must be the oracle's circle-colouring classes in
    the oracle's order; the oracle (FP64) replays its own order; loads agree within
    LOAD_TOL * max load, the tolerance derived for FP32 passes;
@@ -237,28 +237,36 @@ def test_same_order_weighted_and_sumsq(pkg, orc, weighted):
 
 @pytest.mark.parametrize("name,T", [("chunglu_10k", 0), ("chunglu_10k", 3), ("chunglu_10k", 40),
                                     ("cl_small", 25), ("two_cliques", 5)])
-def test_extract_bit_exact_on_gpu_loads(pkg, orc, name, T):
+def test_extract_bit_exact_on_the_oracle_state(pkg, orc, name, T):
+    """The oracle runs T passes in its own order; its splits (cast to FP32) become the GPU
+    handle's state through lowd_set_splits, which re-derives the loads from them.  Both sides
+    then extract from the same FP32 loads (each the FP32 rounding of its FP64 sum of splits),
+    so the load order is decided alike and S* and W(S*) must agree bit for bit."""
+    import torch
     g = _graph(name, False)
+    prune = name != "two_cliques"
     h = _load(pkg, g, True)
-    if name != "two_cliques":
+    if prune:
         pkg.lowd_prune(h)
+    n, u, v, w, idmap = oracle_graph(orc, g, prune)
+    o = orc.LowdState(n, u, v, w)
     if T:
-        pkg.lowd_iterate(h, T)
-    gu, gv, gw = (_np(x) for x in pkg.lowd_get_graph(h))
-    info = pkg.lowd_get_info(h)
-    lg = _np(pkg.lowd_get_loads(h))
+        order, _, _ = orc.circle_order(n, u, v)
+        o.iterate(T, order=order)
+    s32 = o.fu.astype(np.float32)                      # f_e(lo): u < v in the canonical order
+    pkg.lowd_set_splits(h, torch.from_numpy(s32).cuda())
     S, rho, loads = pkg.lowd_extract(h)
-    wu, scale = orc.weight_units(gu.shape[0], None)
-    So, Wo = orc.extract(info["n"], gu, gv, wu, lg.astype(np.float64))
-    # map the oracle's current ids to original ids
-    if info["pruned"]:
-        _, rr = pkg.lowd_get_prune_info(h)
-        idmap = np.nonzero(_np(rr) < 0)[0]
-        So = idmap[So]
-    assert np.array_equal(_np(S), So)
+    l64 = np.zeros(n)
+    np.add.at(l64, u, s32.astype(np.float64))
+    np.add.at(l64, v, 1.0 - s32.astype(np.float64))
+    l32 = l64.astype(np.float32)
+    wu, scale = orc.weight_units(u.shape[0], None)
+    So, Wo = orc.extract(n, u, v, wu, l32.astype(np.float64))
+    assert np.array_equal(_np(S), idmap[So])
     assert rho == Wo / scale / So.shape[0]
     full = _np(loads)
     assert full.shape[0] == g.n
+    assert np.array_equal(full[idmap], l32)
     pkg.lowd_free(h)
 
 
@@ -276,11 +284,13 @@ def test_converged_loads_and_densest_set(pkg, orc, name, weighted, T):
     rho_star, B1 = orc.densest_flow(g.n, g.u, g.v, wu)
     assert abs(rho - float(rho_star) / scale) <= 1e-9 * float(rho_star) / scale
     assert np.array_equal(_np(S), np.nonzero(B1)[0])
-    # converged loads against the exact decomposition of the pruned graph
-    gu, gv, gw = (_np(x) for x in pkg.lowd_get_graph(h))
-    info = pkg.lowd_get_info(h)
-    whu, _ = orc.weight_units(gu.shape[0], None if g.w is None else gw)
-    lstar, shell, lam = orc.ldd_loads(info["n"], gu, gv, whu, scale)
+    # converged loads against the exact decomposition of the pruned graph (the oracle's own
+    # pruning; the GPU's pruned graph must be the same)
+    n, u, v, w, idmap = oracle_graph(orc, g, True)
+    gu, gv, _ = (_np(x) for x in pkg.lowd_get_graph(h))
+    assert np.array_equal(gu, u) and np.array_equal(gv, v)
+    whu, _ = orc.weight_units(u.shape[0], w)
+    lstar, shell, lam = orc.ldd_loads(n, u, v, whu, scale)
     lg = _np(pkg.lowd_get_loads(h)).astype(np.float64)
     assert np.max(np.abs(lg - lstar)) <= 1e-4 * lstar.max()
     # the loads reported in original numbering: zero for pruned nodes
