@@ -14,12 +14,16 @@
 // path serves are dense cores (maximum degree close to n), where P is within a few
 // colours of the lower bound Delta.
 //
-// Execution.  One CTA of 1024 threads keeps every node load in shared memory for all
-// passes of a call and streams the edges of each class (packed 16-bit endpoint pairs
-// when n <= 65536, the FP32 split and, if weighted, the FP32 weight), prefetching the
-// next class's edges into registers while the current class is updated; __syncthreads
-// separates classes.  The split of edge e = (lo, hi) is stored once, s_e = f_e(lo);
-// f_e(hi) = w_e - s_e (the tighter dual's equality f_e(u) + f_e(v) = w_e, Sec. III-B).
+// Execution.  One CTA keeps every node load in shared memory for all passes of a call, as
+// an FP32 pair (hi, lo) updated by error-free transfers (TwoSum), so no update rounds a load.
+// The class segments (packed 16-bit endpoint pairs when n <= 65536, the FP32 split and, if
+// weighted, the FP32 weight) are staged global -> shared in chunks of consecutive classes by
+// a producer warp with cp.async.bulk and mbarriers, and the updated splits go back by bulk
+// stores; the consumer warps touch only shared memory and meet at a named barrier after each
+// class (k_sweep_tma).  Graphs whose staged layout does not fit use a register-prefetch
+// kernel with single FP32 loads (k_sweep_vec, k_sweep_simple).  The split of edge
+// e = (lo, hi) is stored once, s_e = f_e(lo); f_e(hi) = w_e - s_e (the tighter dual's
+// equality f_e(u) + f_e(v) = w_e, Sec. III-B).
 #include "ctx.cuh"
 #include "prims.cuh"
 #include "async.cuh"
