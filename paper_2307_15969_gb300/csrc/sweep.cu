@@ -43,12 +43,14 @@ inline unsigned grid_for(int64_t n) {
 
 // Colour of each edge (the circle colouring) and its place inside the class.  Inside a
 // class every edge pairs a and b = c - a (mod P); with b < P the high end is fixed by the
-// low one and the wrap group g = [a + b >= P], so edges of one group whose low ends lie
-// in distinct shared-memory banks (a mod 32) also have high ends in distinct banks.  The
-// first key orders a class by (group, bank of the low end); the second deals the edges
-// out bank by bank in rounds, so consecutive edges (one warp's accesses) mostly touch
-// 32 different banks at both ends.
+// low one and the wrap group g = [a + b >= P], so edges of one group whose low ends are
+// distinct mod 16 also have high ends distinct mod 16.  The staged sweep keeps a load as an
+// 8-byte pair, and a warp's 8-byte shared-memory access is served half a warp at a time: 16
+// lanes touching nodes distinct mod 16 use all 32 banks once.  The first key orders a class
+// by (group, low end mod 16); the second deals the edges out in rounds of 16, so each half
+// warp's edges mostly have distinct ends mod 16 at both ends.
 constexpr int kRankBits = 16;  // rank inside a (class, group, bank) bucket: < 2^16
+constexpr int kBankBits = 4;   // 16 load slots of 8 bytes span the 32 four-byte banks
 
 __global__ void k_circle_colour(const int32_t* __restrict__ u, const int32_t* __restrict__ v, int64_t m,
                                 int32_t n, uint64_t* __restrict__ key, int32_t* __restrict__ val) {
@@ -59,7 +61,8 @@ __global__ void k_circle_colour(const int32_t* __restrict__ u, const int32_t* __
         const uint32_t a = (uint32_t)u[e], b = (uint32_t)v[e];
         const uint32_t c = (b == Np - 1) ? (2u * a) % P : (a + b) % P;
         const uint32_t g = (b != Np - 1 && a + b >= P) ? 1u : 0u;
-        key[e] = ((uint64_t)c << 6) | ((uint64_t)g << 5) | (uint64_t)(a & 31u);
+        key[e] = ((uint64_t)c << (kBankBits + 1)) | ((uint64_t)g << kBankBits) |
+                 (uint64_t)(a & ((1u << kBankBits) - 1u));
         val[e] = (int32_t)e;
     }
 }
@@ -75,7 +78,8 @@ __global__ void k_bank_rounds(const uint64_t* __restrict__ key, int64_t m, uint6
             if (key[mid] < k) lo = mid + 1; else hi = mid;
         }
         const uint64_t r = (uint64_t)(i - lo);
-        key2[i] = ((k >> 5) << (kRankBits + 5)) | (r << 5) | (k & 31u);
+        key2[i] = ((k >> kBankBits) << (kRankBits + kBankBits)) | (r << kBankBits) |
+                  (k & ((1u << kBankBits) - 1u));
     }
 }
 
@@ -753,16 +757,16 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
             LOWD_LAUNCH(k_circle_colour, grid_for(m), kT, 0, st, h->u, h->v, m, n, key[0], val[0]);
             const uint32_t P = (uint32_t)(n + (n & 1)) - 1u;
             const int cbits = bit_length_u64(P > 0 ? P - 1 : 0);
-            cur = radix_sort_pairs<uint64_t, int32_t>(key[0], val[0], key[1], val[1], m, cbits + 6, h->tmp, st);
+            cur = radix_sort_pairs<uint64_t, int32_t>(key[0], val[0], key[1], val[1], m, cbits + kBankBits + 1, h->tmp, st);
             uint64_t* kA = key[cur];
             int32_t* vA = val[cur];
             uint64_t* kB = key[1 - cur];
             int32_t* vB = val[1 - cur];
             LOWD_LAUNCH(k_bank_rounds, grid_for(m), kT, 0, st, kA, m, kB);
-            const int r2 = radix_sort_pairs<uint64_t, int32_t>(kB, vA, kA, vB, m, cbits + 6 + kRankBits, h->tmp, st);
+            const int r2 = radix_sort_pairs<uint64_t, int32_t>(kB, vA, kA, vB, m, cbits + kBankBits + 1 + kRankBits, h->tmp, st);
             kfin = r2 ? kA : kB;
             vfin = r2 ? vB : vA;
-            LOWD_LAUNCH(k_class_heads, grid_for(m), kT, 0, st, kfin, m, kRankBits + 6, head);
+            LOWD_LAUNCH(k_class_heads, grid_for(m), kT, 0, st, kfin, m, kRankBits + kBankBits + 1, head);
             scan_exclusive<int32_t>(head, hpos, m, h->d_i32 + 5, h->tmp, st);
             if (cudaMemcpyAsync(h->h_pin, h->d_i32 + 5, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                 cudaStreamSynchronize(st) != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
