@@ -9,7 +9,9 @@
 //   schedule: the circle colouring of the core, edges counting-sorted by colour (each
 //     class a matching, so its updates run in parallel);
 //   Algorithm 1: equal split, then `passes` passes of all classes in colour order with the
-//     loads in shared memory and a barrier between classes;
+//     loads in shared memory; classes padded to 4 edges, staged global -> shared in chunks
+//     by the last warp with bulk copies, consumers meeting at a named barrier per class
+//     (an unstaged loop with a CTA barrier per class when the stages do not fit);
 //   extraction: bitonic sort of (load desc, id desc), prefix weights by per-edge buckets
 //     and a scan, the largest k maximising W(S_k)/k.
 // Unit weights only.  Limits: a graph's node count must fit the shared-memory budget
