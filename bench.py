@@ -119,6 +119,20 @@ def _dist():
     return ws, rank, local
 
 
+def replica_throughput(local_seconds: float, local_updates: float, ws: int, device=None):
+    """Whole-job throughput of independent replicas (one per rank, no data exchange): the
+    updates of every rank over the slowest rank's time.  Returns (value, max seconds)."""
+    if ws <= 1:
+        return local_updates / local_seconds, local_seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([local_updates], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
 def cpu_baseline_sample(g, T_target_s: float = 12.0):
     """The oracle as it stands on this host: its own pruning of G, then LOWD passes on H
     for roughly T_target_s seconds.  Returns (updates/s, dict)."""
@@ -324,14 +338,8 @@ def main():
             torch.distributed.barrier()
         ck = clocks.stop()
 
-        total = sum(times)
-        if ws > 1:
-            t = torch.tensor([total], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
         m_H = info["m_H"]
-        updates = m_H * T * args.steps * ws
-        value = updates / total
+        value, total = replica_throughput(sum(times), float(m_H * T * args.steps), ws, dev)
 
         # the dominant kernel: the one-CTA LOWD sweep; its launch duration from events
         # around lowd_iterate(T) minus lowd_iterate(0) (re-derivation only)
