@@ -19,7 +19,7 @@ from _oracle_side import assert_same_schedule, oracle_graph
 
 pytestmark = pytest.mark.gpu
 
-LOAD_TOL = 1e-4   # relative to the largest load; FP32 passes, see the design doc
+LOAD_TOL = 1e-4   # relative to the largest load: the bar for converged loads, scaled below
 
 
 def load_tol(T):
