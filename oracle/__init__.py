@@ -62,6 +62,8 @@ def _load():
         lib.orc_ldd.restype = i32
         lib.orc_ldd.argtypes = [i32, i64, P, P, P, P, P, P]
         lib.orc_load_stats.argtypes = [i32, P, P]
+        lib.orc_level_colouring.restype = i32
+        lib.orc_level_colouring.argtypes = [i32, i64, P, P, P]
         _lib = lib
     return _lib
 
@@ -229,6 +231,36 @@ def circle_order(n, u, v):
     colour = np.where(b == Np - 1, (2 * a) % P, (a + b) % P)
     order = np.argsort(colour, kind="stable").astype(np.int32)
     offs = np.searchsorted(colour[order], np.arange(P + 1)).astype(np.int64)
+    return order, offs, colour
+
+
+def level_order(n, u, v):
+    """The pass order of the streamed schedule (graphs of any size), from its definition.
+
+    Edges are ranked by the key (max(d_a, d_b), min(d_a, d_b), fmix32(edge id)), d the
+    unweighted degree (light edges first; fmix32, MurmurHash3's 32-bit finaliser, a
+    bijection, scrambles ties).  Visiting them in that order is one valid pass of Algorithm 1
+    (the paper allows any order, Fig. 1 caption).  Its colour classes group the edges by
+    level: colour(e) = 1 + max colour of the edges sharing an endpoint with e that come
+    earlier in key order (0 if none).  Each class is a matching, and visiting the classes in
+    ascending colour keeps the key order at every node, so it gives the same pass.
+    Returns (order, class_offsets[C + 1], colour): order lists edge ids class by class, by
+    edge id inside a class.
+
+    Parity pinned by tests/test_oracle_schedule.py: the literal round process (every node
+    designates its first uncoloured edge by key; an edge designated by both ends takes the
+    round's colour) gives the same colours on random graphs; classes are matchings; stars,
+    paths and cliques give their closed-form colour counts."""
+    lib = _load()
+    u = _c(u, np.int32); v = _c(v, np.int32)
+    m = u.shape[0]
+    colour = np.zeros(max(m, 1), np.int32)
+    C = lib.orc_level_colouring(int(n), m, _p(u), _p(v), _p(colour))
+    if C < 0:
+        raise MemoryError
+    colour = colour[:m]
+    order = np.argsort(colour, kind="stable").astype(np.int32)
+    offs = np.searchsorted(colour[order], np.arange(C + 1)).astype(np.int64)
     return order, offs, colour
 
 

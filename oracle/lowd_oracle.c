@@ -22,6 +22,8 @@
  *   orc_lowd_init      equal split, initial loads                       [Alg. 1 init]
  *   orc_lowd_iterate   T passes of the edge loop in a given edge order  [Alg. 1]
  *   orc_extract        argsort by load, peel lowest, best prefix        [Alg. 1 extraction]
+ *   orc_level_colouring  pass order for graphs of any size (conflict-free batches; the
+ *                      paper visits edges in any order, Fig. 1 caption)
  *   orc_greedy         Charikar peeling (test-only cross-check)         [Alg. 3]
  *   orc_densest_flow   exact rho* and maximal densest set by min cut    [Sec. I, Goldberg]
  *   orc_ldd            exact locally-dense decomposition by min cuts    [Sec. II, Def. LDD]
@@ -612,3 +614,71 @@ void orc_load_stats(int32_t n, const double* l, double* out3) {
     for (int32_t x = 0; x < n; ++x) { s += l[x]; s2 += l[x] * l[x]; if (l[x] > mx) mx = l[x]; }
     out3[0] = s; out3[1] = s2; out3[2] = n > 0 ? mx : 0.0;
 }
+
+/* ------------------------------------------------------------------ pass order (any size) */
+
+typedef struct { uint64_t key; uint32_t tie; int64_t e; } edgekey;
+
+static int cmp_edgekey(const void* x, const void* y) {
+    const edgekey* a = (const edgekey*)x;
+    const edgekey* b = (const edgekey*)y;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    if (a->tie != b->tie) return a->tie < b->tie ? -1 : 1;
+    return a->e < b->e ? -1 : (a->e > b->e);
+}
+
+/* The 32-bit finaliser of Appleby's MurmurHash3 (fmix32), a bijection on 32-bit words:
+ * it orders edges of equal degree key in a scrambled, fixed order. */
+static uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+/* A proper edge colouring whose colour classes, visited in ascending colour, give a pass
+ * of Algorithm 1 in the order "edges by ascending key" (any order is allowed, Fig. 1
+ * caption): edges sharing an endpoint keep their key order, and edges with no endpoint in
+ * common commute.  The key of e = (a, b) is (max(d_a, d_b), min(d_a, d_b), fmix32(e)), d the
+ * unweighted degree: light edges first, so early classes are large and the long tail of
+ * classes holds the edges of the highest-degree nodes.  Ties of degree are broken by a
+ * scrambled edge id, not the id itself: edges listed in id order along a path or a chain
+ * of equal-degree nodes would otherwise each wait for the previous one.
+ *
+ * colour(e) = 1 + the largest colour among the edges that share an endpoint with e and come
+ * before it in key order (0 if there is none): the level of e in that dependency order.  Two
+ * edges at one node differ in colour, so every class is a matching; a node of degree d has
+ * d edges with distinct colours, so there are at least max d colours.  Scanning the edges in
+ * key order, the largest earlier colour at a node is the colour of its latest edge so far.
+ * Writes colour[e]; returns the number of colours, or -1 on allocation failure. */
+int32_t orc_level_colouring(int32_t n, int64_t m, const int32_t* u, const int32_t* v,
+                            int32_t* colour) {
+    int64_t* deg = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    edgekey* k = (edgekey*)malloc(sizeof(edgekey) * (size_t)(m + 1));
+    int32_t* last = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    if (!deg || !k || !last) { free(deg); free(k); free(last); return -1; }
+    for (int64_t e = 0; e < m; ++e) { deg[u[e]]++; deg[v[e]]++; }
+    for (int64_t e = 0; e < m; ++e) {
+        uint64_t da = (uint64_t)deg[u[e]], db = (uint64_t)deg[v[e]];
+        uint64_t hi = da > db ? da : db, lo = da > db ? db : da;
+        k[e].key = (hi << 32) | lo;
+        k[e].tie = fmix32((uint32_t)e);
+        k[e].e = e;
+    }
+    qsort(k, (size_t)m, sizeof(edgekey), cmp_edgekey);
+    for (int32_t x = 0; x < n; ++x) last[x] = -1;
+    int32_t C = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t e = k[i].e;
+        int32_t c = (last[u[e]] > last[v[e]] ? last[u[e]] : last[v[e]]) + 1;
+        colour[e] = c;
+        last[u[e]] = c;
+        last[v[e]] = c;
+        if (c + 1 > C) C = c + 1;
+    }
+    free(deg); free(k); free(last);
+    return C;
+}
+
