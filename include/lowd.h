@@ -104,6 +104,10 @@ typedef struct {
     int32_t schedule;     /* schedule in use: 1 one-CTA shared memory, 2 grid matchings */
     int32_t max_degree;   /* maximum (unweighted) degree of the current graph */
     int32_t prune_rounds; /* rounds lowd_prune ran */
+    int32_t sweep_kernel; /* kernel of the last pass: 0 none yet, 1 staged one-CTA sweep with
+                             pair loads, 2 one-CTA register-ring sweep, 3 one-CTA simple
+                             sweep, 4 streamed sweep (schedule 2, loads in global memory) */
+    int32_t sweep_edges_per_thread; /* edges per consumer thread per class of kernel 1 */
 } lowd_info;
 
 /*
@@ -248,14 +252,19 @@ lowd_status lowd_get_edge_order(lowd_handle h, int32_t* perm, int32_t* class_off
  * device memory belongs to its own pool allocator, or a loop with a fixed memory budget
  * that cannot absorb the device-wide synchronisation cudaMalloc/cudaFree may cause.
  *   n, m       nodes (1 <= n <= 65536) and edges (0 <= m < 2^31)
- *   u, v       device int32 [m]: edge ends, each pair listed once, ids in [0, n)
- *   w          device float [m] weights, or NULL for unit weights; each weight counts as
- *              its nearest multiple of 2^-20 (at least 2^-20), as in lowd_load_graph
+ *   u, v       device int32 [m]: edge ends, each pair listed once, ids in [0, n), u != v
+ *   w          device float [m] weights, or NULL for unit weights; each weight must be
+ *              positive and finite and counts as its nearest multiple of 2^-20 (at least
+ *              2^-20), as in lowd_load_graph; it must also stay below 2^62 / m units of
+ *              2^-20 so that the prefix sums are exact 64-bit integers
  *   loads      device float [n]: node loads (e.g. from lowd_get_loads)
  *   S          device int32 [n] out: ids of S* ascending, or NULL
  *   S_size     host out: |S*|;   rho   host out: W(S*)/|S*|
  *   stream     cudaStream_t (as void*); the call synchronises it before returning
  * Returns LOWD_ERR_TOO_LARGE when n > 65536 and LOWD_ERR_INVALID_ARG on bad arguments.
+ * The arrays are checked on the GPU: an edge with an id outside [0, n), a self-loop or a
+ * weight outside the rules above is skipped (never read past the arrays) and the call
+ * returns LOWD_ERR_INVALID_ARG; S, S_size and rho are then not valid.
  * All intermediate buffers come from one static device array of 4 MiB that every GPU
  * which loads this library holds until the process exits.  Its device address is looked
  * up (cudaGetSymbolAddress) on the first call made on each device, with that device

@@ -9,6 +9,24 @@ static std::atomic<unsigned long long> g_launches{0};
 
 void lowd_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+int lowd_device_sms() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];   // 0 = not yet queried
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return 148;   // a conservative count if the device cannot be queried
+    }
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+        cudaGetLastError();
+        return 148;
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
+
 namespace {
 
 lowd_status check_handle(lowd_handle h) { return h ? LOWD_OK : LOWD_ERR_INVALID_ARG; }
@@ -80,12 +98,7 @@ __global__ void k_half_weights(const float* __restrict__ w, int64_t m, float* __
         out[e] = w ? 0.5f * w[e] : 0.5f;
 }
 
-inline unsigned grid_for(int64_t n) {
-    int64_t b = (n + 255) / 256;
-    if (b > 152 * 32) b = 152 * 32;
-    if (b < 1) b = 1;
-    return (unsigned)b;
-}
+inline unsigned grid_for(int64_t n) { return lowd_grid_for(n, 256); }
 
 // loads of the current graph into a fresh device buffer (equal-split loads before any pass)
 lowd_status current_loads(lowd_ctx* h, float** out) {
@@ -300,6 +313,8 @@ lowd_status lowd_get_info(lowd_handle h, lowd_info* info) {
     x.schedule = h->sched;
     x.max_degree = h->max_deg;
     x.prune_rounds = h->prune_rounds;
+    x.sweep_kernel = h->sweep_kernel;
+    x.sweep_edges_per_thread = h->sweep_E;
     *info = x;
     return LOWD_OK;
 }

@@ -731,9 +731,7 @@ lowd_status lowd_batch_create(int32_t B, const int64_t* node_off, const int64_t*
         }
         cudaMemsetAsync(b->queue, 0, 16 * sizeof(int32_t), b->st);
         if (m > 0) {
-            int64_t grid = ((int64_t)m + 255) / 256;
-            if (grid > 152 * 32) grid = 152 * 32;
-            LOWD_LAUNCH(k_batch_check, (unsigned)grid, 256, 0, b->st, b->node_off, b->edge_off, B, b->u, b->v,
+            LOWD_LAUNCH(k_batch_check, lowd_grid_for((int64_t)m, 256), 256, 0, b->st, b->node_off, b->edge_off, B, b->u, b->v,
                         (int64_t)m, b->queue + 8);
         }
         int32_t bad = 0;

@@ -49,6 +49,8 @@ struct lowd_ctx {
     int inited = 0;
     int32_t iters = 0;
     int sched = 0;             // 1 one-CTA shared memory, 2 grid matchings
+    int sweep_kernel = 0;      // kernel of the last pass (lowd_info.sweep_kernel)
+    int sweep_E = 0;           // edges per consumer thread of the staged sweep
     int32_t C = 0;             // number of classes
     int64_t m_pad = 0;         // class-major length, each class padded to a multiple of 4
     int32_t* perm = nullptr;   // [m_pad] class-major position -> canonical edge id, -1 = padding

@@ -16,12 +16,7 @@ namespace {
 
 constexpr int kT = 256;
 
-inline unsigned grid_for(int64_t n) {
-    int64_t b = (n + kT - 1) / kT;
-    if (b > 152 * 32) b = 152 * 32;
-    if (b < 1) b = 1;
-    return (unsigned)b;
-}
+inline unsigned grid_for(int64_t n) { return lowd_grid_for(n, kT); }
 
 // descending-load key: larger load -> smaller key; values start as n-1..0 so that the
 // stable sort leaves equal loads in descending id order
@@ -190,18 +185,15 @@ lowd_status lowd_extract_best(lowd_ctx* h, const float* loads_dev, int32_t* S_de
 // process on every device that loads this library, so its size is kept small: graphs of
 // at most LOWD_NOALLOC_MAX_NODES nodes.
 
-#include <mutex>
-
 namespace {
 
 constexpr int32_t kNoallocMaxNodes = LOWD_NOALLOC_MAX_NODES;
-constexpr int kNoallocMaxDevices = 64;
 
 inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // carve-up of the scratch array for n nodes (byte offsets, each 256-aligned)
 struct NoallocLayout {
-    size_t key0, key1, val0, val1, pos, bucket, excl, flag, fpos, part, tmp, total;
+    size_t bad, key0, key1, val0, val1, pos, bucket, excl, flag, fpos, part, tmp, total;
 };
 
 constexpr size_t noalloc_part_entries() {
@@ -212,6 +204,7 @@ inline NoallocLayout noalloc_layout(int32_t n) {
     NoallocLayout L{};
     size_t o = 0;
     const size_t nn = (size_t)(n > 0 ? n : 1);
+    L.bad = o; o = al256(o + 4);
     L.key0 = o; o = al256(o + 4 * nn);
     L.key1 = o; o = al256(o + 4 * nn);
     L.val0 = o; o = al256(o + 4 * nn);
@@ -232,40 +225,46 @@ inline NoallocLayout noalloc_layout(int32_t n) {
 constexpr size_t kNoallocScratchBytes = (size_t)4 << 20;  // 4 MiB
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
-
-// Device address of the scratch on the current device, looked up once per device.
+// Device address of the scratch on the current device.  It is looked up on every call:
+// after cudaDeviceReset the module is loaded again and the array may sit elsewhere, so a
+// cached address could be stale.
 cudaError_t noalloc_scratch(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
-// weight of each edge in 2^-20 units, rounded as lowd_load_graph rounds it
+// Bits of the input-check word of the allocation-free extraction.
+enum { NA_RANGE = 1, NA_LOOP = 2, NA_WEIGHT = 4 };
+
+// Each edge's weight in 2^-20 units, rounded as lowd_load_graph rounds it, added to the
+// bucket of the later of its ends.  The caller's arrays are not trusted: an edge with an end
+// outside [0, n), a self-loop, or a weight that is not positive and finite or that would let
+// the int64 prefix sums overflow (2^-20 units >= wmax_units) is skipped and flagged in *bad.
 __global__ void k_edge_buckets_f32(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
-                                   const float* __restrict__ w, int64_t m, const int32_t* __restrict__ pos,
-                                   unsigned long long* __restrict__ bucket) {
+                                   const float* __restrict__ w, int64_t m, int32_t n, double wmax_units,
+                                   const int32_t* __restrict__ pos, unsigned long long* __restrict__ bucket,
+                                   int32_t* __restrict__ bad) {
+    int flags = 0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t p = max(pos[u[e]], pos[v[e]]);
+        const int32_t a = u[e], b = v[e];
+        if (a < 0 || a >= n || b < 0 || b >= n) { flags |= NA_RANGE; continue; }
+        if (a == b) { flags |= NA_LOOP; continue; }
         unsigned long long x = 1ull;
         if (w) {
-            const double y = rint((double)w[e] * 1048576.0);
+            const float wf = w[e];
+            if (!(wf > 0.0f) || !isfinite(wf)) { flags |= NA_WEIGHT; continue; }
+            const double y = rint((double)wf * 1048576.0);
+            if (!(y < wmax_units)) { flags |= NA_WEIGHT; continue; }
             x = y < 1.0 ? 1ull : (unsigned long long)y;
         }
-        atomicAdd(&bucket[p], x);
+        atomicAdd(&bucket[max(pos[a], pos[b])], x);
     }
+    flags = __reduce_or_sync(0xffffffffu, flags);
+    if (flags && lane_id() == 0) atomicOr(bad, flags);
 }
 
 }  // namespace
@@ -296,13 +295,19 @@ extern "C" lowd_status lowd_extract_noalloc(int32_t n, int64_t m, const int32_t*
     int32_t* fpos = (int32_t*)(b + lay.fpos);
     Best* part = (Best*)(b + lay.part);
     void* tmp = b + lay.tmp;
+    int32_t* bad = (int32_t*)(b + lay.bad);
     const unsigned nb = grid_for(n);
-    // the array keeps the previous call's contents: the buckets must start at zero
+    // the array keeps the previous call's contents: the buckets and the check word must
+    // start at zero
     cudaMemsetAsync(bucket, 0, sizeof(unsigned long long) * (size_t)n, st);
+    cudaMemsetAsync(bad, 0, sizeof(int32_t), st);
+    // per-edge weight bound: m edges of < 2^62 / m units each keep every prefix sum and the
+    // 128-bit density products exact
+    const double wmax_units = m > 0 ? 4611686018427387904.0 / (double)m : 0.0;
     LOWD_LAUNCH(k_load_keys, grid_for(n), kT, 0, st, loads, n, key0, val0);
     const int cur = radix_sort_pairs<uint32_t, int32_t>(key0, val0, key1, val1, n, 32, tmp, st);
     LOWD_LAUNCH(k_positions, grid_for(n), kT, 0, st, cur ? val1 : val0, n, pos);
-    if (m > 0) LOWD_LAUNCH(k_edge_buckets_f32, grid_for(m), kT, 0, st, u, v, w, m, pos, bucket);
+    if (m > 0) LOWD_LAUNCH(k_edge_buckets_f32, grid_for(m), kT, 0, st, u, v, w, m, n, wmax_units, pos, bucket, bad);
     scan_exclusive<int64_t>((const int64_t*)bucket, excl, n, nullptr, tmp, st);
     LOWD_LAUNCH(k_best_prefix, nb, kT, 0, st, excl, bucket, n, part);
     LOWD_LAUNCH(k_best_final, 1, 32, 0, st, part, (int32_t)nb, part + nb);
@@ -310,13 +315,16 @@ extern "C" lowd_status lowd_extract_noalloc(int32_t n, int64_t m, const int32_t*
     scan_exclusive<int32_t>(flag, fpos, n, nullptr, tmp, st);
     if (S) LOWD_LAUNCH(k_emit_members, grid_for(n), kT, 0, st, flag, fpos, n, nullptr, S);
     Best best;
+    int32_t badw = 0;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&best, part + nb, sizeof(Best), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&badw, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return LOWD_ERR_CUDA;
     }
+    if (badw) return LOWD_ERR_INVALID_ARG;   // S (if given) holds a result of the valid edges only
     *S_size = (int32_t)best.k;
     const double scale = w ? 1048576.0 : 1.0;
     *rho = best.k > 0 ? (double)best.W / scale / (double)best.k : 0.0;

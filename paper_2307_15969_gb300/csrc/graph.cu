@@ -236,12 +236,7 @@ __global__ void k_emit_edges(const int32_t* __restrict__ u, const int32_t* __res
     }
 }
 
-inline unsigned grid_for(int64_t n) {
-    int64_t b = (n + kT - 1) / kT;
-    if (b > 152 * 32) b = 152 * 32;
-    if (b < 1) b = 1;
-    return (unsigned)b;
-}
+inline unsigned grid_for(int64_t n) { return lowd_grid_for(n, kT); }
 
 }  // namespace
 

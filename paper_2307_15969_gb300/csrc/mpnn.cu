@@ -41,17 +41,11 @@ __host__ __device__ constexpr int64_t off_b(int l) { return off_W(l) + (int64_t)
 constexpr int64_t kOffQ = kIn * kH + kH + kL * kLayerParams;
 constexpr int kT = 256;
 constexpr int kWarpsPerBlock = kT / 32;
-constexpr int kGridCap = 152 * 16;
 constexpr uint32_t kUmmaWaitLimit = 1u << 24;
 constexpr int kUmmaSmem = 56 * 1024;   // caps residency at 4 CTAs per SM: <= 512 TMEM columns
 constexpr int kUmmaCtasPerSm = 4;
 
-inline unsigned blocks_for(int64_t items, int per) {
-    int64_t b = (items + per - 1) / per;
-    if (b > kGridCap) b = kGridCap;
-    if (b < 1) b = 1;
-    return (unsigned)b;
-}
+inline unsigned blocks_for(int64_t items, int per) { return lowd_grid_for(items, per, 16); }
 
 __device__ __forceinline__ float wt(const float* w, int64_t e) { return w ? w[e] : 1.0f; }
 

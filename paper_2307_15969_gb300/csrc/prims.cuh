@@ -10,6 +10,19 @@
 // Host-side count of kernel launches made by this library (all threads, all handles).
 void lowd_note_launch();
 
+// Streaming multiprocessors of the current device (queried once per device ordinal).
+int lowd_device_sms();
+
+// Blocks for a grid-stride loop over n items at `threads` per block: enough to cover n,
+// at most `per_sm` blocks per SM of the current device.
+inline unsigned lowd_grid_for(int64_t n, int threads, int per_sm = 32) {
+    int64_t b = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)lowd_device_sms() * per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
 // Launch a kernel and count it.
 #define LOWD_LAUNCH(kern, grid, block, smem, stream, ...)              \
     do {                                                               \

@@ -34,12 +34,7 @@ namespace {
 
 constexpr int kT = 256;
 
-inline unsigned grid_for(int64_t n) {
-    int64_t b = (n + kT - 1) / kT;
-    if (b > 152 * 32) b = 152 * 32;
-    if (b < 1) b = 1;
-    return (unsigned)b;
-}
+inline unsigned grid_for(int64_t n) { return lowd_grid_for(n, kT); }
 
 // Colour of each edge (the circle colouring) and its place inside the class.  Inside a
 // class every edge pairs a and b = c - a (mod P); with b < P the high end is fixed by the
@@ -658,6 +653,8 @@ cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* 
     if (threads < 64) threads = 64;
     if (threads > kTmaConsumers) threads = kTmaConsumers;
     auto kern = E == 4 ? k_sweep_tma<WEIGHTED, 4> : (E == 2 ? k_sweep_tma<WEIGHTED, 2> : k_sweep_tma<WEIGHTED, 1>);
+    h->sweep_kernel = 1;
+    h->sweep_E = E;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
     if (e != cudaSuccess) return e;
     const int32_t per = (int32_t)(0x7fffffff / NC);
@@ -697,11 +694,15 @@ cudaError_t launch_sweep(lowd_ctx* h, int32_t passes) {
     constexpr int kRing = WEIGHTED ? kRingW : kRingU;
     if (h->C >= kRing) {
         auto kern = co_smem ? k_sweep_vec<WEIGHTED, kRing, true> : k_sweep_vec<WEIGHTED, kRing, false>;
+        h->sweep_kernel = 2;
+        h->sweep_E = 0;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         LOWD_LAUNCH(kern, 1, threads, smem, h->st, h->n, h->C, h->coff, cuv, cw, cs, h->l, h->l_lo, passes);
     } else {
         auto kern = k_sweep_simple<WEIGHTED>;
+        h->sweep_kernel = 3;
+        h->sweep_E = 0;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lbytes);
         if (e != cudaSuccess) return e;
         LOWD_LAUNCH(kern, 1, threads, lbytes, h->st, h->n, h->C, h->coff, cuv, cw, cs, h->l, h->l_lo, passes);

@@ -64,7 +64,8 @@ class lowd_info(C.Structure):
     _fields_ = [("n_orig", C.c_int32), ("n", C.c_int32), ("m_orig", C.c_int64), ("m", C.c_int64),
                 ("duplicates", C.c_int64), ("weighted", C.c_int32), ("pruned", C.c_int32),
                 ("classes", C.c_int32), ("schedule", C.c_int32), ("max_degree", C.c_int32),
-                ("prune_rounds", C.c_int32)]
+                ("prune_rounds", C.c_int32), ("sweep_kernel", C.c_int32),
+                ("sweep_edges_per_thread", C.c_int32)]
 
 
 class lowd_batch_options(C.Structure):

@@ -105,3 +105,56 @@ def test_batch_rejects_non_canonical_input(setup):
     u3[6], v3[6] = u3[5], v3[5]      # a repeated pair
     with pytest.raises(pkg.LowdError):
         pkg.lowd_batch_create(node_off, edge_off, u3, v3)
+
+
+@pytest.fixture(scope="module")
+def top_of_range():
+    """Graphs of the batched recipe at the top of its size range (n in [18,000, 20,000]:
+    ~0.5 M edges, pruned cores of ~1,000 nodes and ~240 k edges, the largest the workload
+    makes), interleaved with small ones so that uneven graphs share the launch."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    oracle.build()
+    big = synth.batch(8, seed_base=7000, n_lo=18000, n_hi=20000)
+    small = synth.batch(4, seed_base=7100, n_hi=600)
+    graphs = [x for pair in zip(big[:4], small) for x in pair] + big[4:]
+    node_off = np.concatenate([[0], np.cumsum([g.n for g in graphs])]).astype(np.int64)
+    edge_off = np.concatenate([[0], np.cumsum([g.m for g in graphs])]).astype(np.int64)
+    u = np.concatenate([g.u for g in graphs]).astype(np.int32)
+    v = np.concatenate([g.v for g in graphs]).astype(np.int32)
+    ref = []
+    for g in graphs:
+        wu = np.ones(g.m, np.int64)
+        pr = oracle.prune(g.n, g.u, g.v, wu, False)
+        keep = pr["removal_round"] < 0
+        rho, B1 = oracle.densest_flow(g.n, g.u, g.v, wu)
+        ref.append(dict(rounds=pr["rounds"], n_core=int(keep.sum()),
+                        m_core=int((keep[g.u] & keep[g.v]).sum()), rho=float(rho), B1=B1, keep=keep))
+    return graphs, node_off, edge_off, u, v, ref
+
+
+def test_batch_top_of_size_range(setup, top_of_range):
+    import oracle as orc
+    pkg = setup[0]
+    graphs, node_off, edge_off, u, v, ref = top_of_range
+    assert max(g.n for g in graphs) >= 19000
+    b = pkg.lowd_batch_create(node_off, edge_off, u, v)
+    for per, thr in ((1, 1024), (2, 512)):
+        pkg.lowd_batch_run(b, passes=400, ctas_per_sm=per, threads=thr)
+        _check(pkg.lowd_batch_results(b), graphs, node_off, ref)
+    # same-order loads after 2 passes (the oracle prunes, compacts and orders each core)
+    pkg.lowd_batch_run(b, passes=2, ctas_per_sm=2, threads=512)
+    res = pkg.lowd_batch_results(b)
+    lg = pkg.lowd_batch_loads(b)
+    for i, g in enumerate(graphs):
+        assert res["status"][i] == 0, i
+        nh, uh, vh, _, idmap = oracle_graph(orc, g, True)
+        order, _, _ = orc.circle_order(nh, uh, vh)
+        o = orc.LowdState(nh, uh, vh)
+        o.iterate(2, order=order)
+        li = lg[node_off[i]:node_off[i + 1]].astype(np.float64)
+        err = np.max(np.abs(li[idmap] - o.l)) if nh else 0.0
+        assert err <= 1e-4 * max(1.0, o.l.max() if nh else 1.0), (i, err)
+    pkg.lowd_batch_free(b)

@@ -19,12 +19,31 @@ from _oracle_side import assert_same_schedule, oracle_graph
 
 pytestmark = pytest.mark.gpu
 
-LOAD_TOL = 1e-4   # relative to the largest load: the bar for converged loads, scaled below
+LOAD_TOL = 1e-4   # relative: the bar for converged loads against the unique optimum
+PAIR_TOL = 1e-6   # relative to the largest load: same-order bar of the pair-load kernels
+FP32_TOL = 1e-4   # relative to the largest load: same-order bar of the single-FP32 kernels
+SUMSQ_RISE = 1e-10  # largest relative rise of sum(l^2) between checks (rounding only)
 
 
-def load_tol(T):
-    """Same-order iterates: accumulated FP32 rounding grows like sqrt(passes)."""
-    return LOAD_TOL * max(1.0, (T / 100.0) ** 0.5)
+def load_tol(T, kernel=1):
+    """Same-order iterates against the FP64 replay, relative to the largest load.
+
+    Kernels 1 and 4 keep every load as an FP32 pair updated by error-free transfers, so a
+    load is the exact sum of what moved; only the FP32 splits round (by at most 2^-24 w_e per
+    update) and the loads are re-derived from them every 50 passes.  The difference from the
+    FP64 run then behaves like a random walk over passes: measured 6e-8 after 1 pass and
+    3.4e-7 after 400 on the weighted R-MAT core, so 1e-6 * sqrt(T/100) leaves a margin of 6
+    to 16.  Kernels 2 and 3 keep single FP32 loads, which round at every update (2^-24 l per
+    update, thousands of updates per node and pass): 1e-4 * sqrt(T/100)."""
+    base = PAIR_TOL if kernel in (1, 4) else FP32_TOL
+    return base * max(1.0, (T / 100.0) ** 0.5)
+
+
+def per_node_converged_ok(lg, lstar):
+    """Converged loads within 1e-4 relative of the unique optimum, node by node."""
+    lg = np.asarray(lg, np.float64)
+    lstar = np.asarray(lstar, np.float64)
+    return np.abs(lg - lstar) <= LOAD_TOL * np.abs(lstar) + 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -198,7 +217,9 @@ def test_same_order_loads(pkg, orc, name, prune, T):
         assert np.unique(ends).shape[0] == ends.shape[0]
     lg = _np(pkg.lowd_get_loads(h)).astype(np.float64)
     scale = max(1.0, o.l.max())
-    assert np.max(np.abs(lg - o.l)) <= load_tol(T) * scale
+    kern = pkg.lowd_get_info(h)["sweep_kernel"]
+    assert kern in (1, 2, 3, 4)
+    assert np.max(np.abs(lg - o.l)) <= load_tol(T, kern) * scale
     sg = _np(pkg.lowd_get_splits(h)).astype(np.float64)
     assert np.all(sg >= 0) and np.all(sg <= 1.0)
     # conservation of the FP32 state: sum of loads equals the number of edges
@@ -224,10 +245,13 @@ def test_same_order_weighted_and_sumsq(pkg, orc, weighted):
             order = assert_same_schedule(orc, n, u, v, *(_np(x) for x in pkg.lowd_get_edge_order(h)))
         o.iterate(5, order=order)
         lg = _np(pkg.lowd_get_loads(h)).astype(np.float64)
-        assert np.max(np.abs(lg - o.l)) <= LOAD_TOL * max(1.0, o.l.max())
-        # sum of squared loads falls monotonically (Sec. III-C), up to FP32 rounding
+        kern = pkg.lowd_get_info(h)["sweep_kernel"]
+        assert np.max(np.abs(lg - o.l)) <= load_tol(5 * (t + 1), kern) * max(1.0, o.l.max())
+        # sum of squared loads falls monotonically (Sec. III-C); the FP32 splits can only
+        # make it rise where an update's gap is below the loads' rounding error, by at most
+        # that error squared per update (about 1e-14 relative per pass here)
         if prev is not None:
-            assert st["sum_load_sq"] <= prev * (1 + 1e-6)
+            assert st["sum_load_sq"] <= prev * (1 + SUMSQ_RISE)
         prev = st["sum_load_sq"]
         assert abs(st["sum_load"] - float(gw.astype(np.float64).sum())) <= 1e-6 * st["sum_load"]
     pkg.lowd_free(h)
@@ -292,7 +316,8 @@ def test_converged_loads_and_densest_set(pkg, orc, name, weighted, T):
     whu, _ = orc.weight_units(u.shape[0], w)
     lstar, shell, lam = orc.ldd_loads(n, u, v, whu, scale)
     lg = _np(pkg.lowd_get_loads(h)).astype(np.float64)
-    assert np.max(np.abs(lg - lstar)) <= 1e-4 * lstar.max()
+    ok = per_node_converged_ok(lg, lstar)
+    assert np.all(ok), (int((~ok).sum()), float(np.max(np.abs(lg - lstar) / lstar)))
     # the loads reported in original numbering: zero for pruned nodes
     _, rr = pkg.lowd_get_prune_info(h)
     full = _np(loads)
