@@ -63,6 +63,16 @@ struct lowd_ctx {
     float* l = nullptr;        // [n + 1] loads; slot n is the padding sentinel
     float* l_lo = nullptr;     // [n + 1] low parts: the load is l + l_lo (pair arithmetic in the sweep)
 
+    // streamed schedule (2): chunked class-major stream, loads in global memory
+    int32_t s2_NC = 0, s2_E = 0, s2_S = 0, s2_D = 0;   // chunks, edges per stage, stages, lead
+    int32_t* s2_ctab = nullptr;   // [NC][20] chunk headers
+    int32_t* s2_beg = nullptr;    // [NC + 1] padded chunk begins
+    int32_t* s2_ea = nullptr;     // [m_pad] ends (node n for padding)
+    int32_t* s2_eb = nullptr;
+    uint32_t* s2_srcA = nullptr;  // [m_pad] read descriptors of the two ends
+    uint32_t* s2_srcB = nullptr;
+    float2* s2_lp = nullptr;      // [n + 1] loads as (hi, lo) pairs during the passes
+
     // scratch
     void* tmp = nullptr;
     size_t tmp_cap = 0;
@@ -134,6 +144,11 @@ lowd_status lowd_sweep_rederive(lowd_ctx* h, double* stats3);
 lowd_status lowd_sweep_splits_canonical(lowd_ctx* h, float* out_dev);
 lowd_status lowd_sweep_load_canonical(lowd_ctx* h, const float* splits_dev);
 lowd_status lowd_sweep_edge_order(lowd_ctx* h, int32_t* out_dev);
+
+// stream.cu
+lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon);
+lowd_status lowd_stream_rederive(lowd_ctx* h, double* L64);
+cudaError_t lowd_stream_passes(lowd_ctx* h, int32_t passes);
 
 // api.cu
 lowd_status lowd_apply_splits_dev(lowd_ctx* h, const float* splits_canon_dev);

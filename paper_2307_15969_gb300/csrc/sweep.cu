@@ -714,6 +714,7 @@ cudaError_t run_passes(lowd_ctx* h, int32_t passes) {
     if (passes <= 0 || h->m == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(h->d_i32 + 8, 0, sizeof(int32_t), h->st);
     if (e != cudaSuccess) return e;
+    if (h->sched == 2) return lowd_stream_passes(h, passes);
     return h->cw ? launch_sweep<true>(h, passes) : launch_sweep<false>(h, passes);
 }
 
@@ -725,10 +726,10 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
     cudaStream_t st = h->st;
     const int64_t m = h->m;
     const int32_t n = h->n;
-    if (schedule_req == 2) {
-        snprintf(h->err, sizeof(h->err), "the grid schedule is not part of this build");
-        return LOWD_ERR_TOO_LARGE;
-    }
+    // schedule 2 (streamed, loads in global memory) when asked for, or automatically when
+    // the loads do not fit the one-CTA sweep's shared memory
+    if (schedule_req == 2 || (schedule_req == 0 && n > LOWD_SMEM_NODES))
+        return lowd_stream_prepare(h, init_splits_canon);
     if (n > LOWD_SMEM_NODES) {
         snprintf(h->err, sizeof(h->err), "current graph has %d nodes; the shared-memory sweep holds at most %d",
                  n, LOWD_SMEM_NODES);
@@ -822,7 +823,12 @@ lowd_status lowd_sweep_rederive(lowd_ctx* h, double* stats3) {
     LOWD_TRY(dalloc(h, &L64, h->n));
     cudaMemsetAsync(L64, 0, sizeof(double) * (size_t)h->n, st);
     cudaMemsetAsync(h->d_stats, 0, 3 * sizeof(double), st);
-    if (h->m_pad > 0) LOWD_LAUNCH(k_rederive, grid_for(h->m_pad), kT, 0, st, h->m_pad, h->cuv, h->cw, h->cs, L64);
+    if (h->sched == 2) {
+        lowd_status r = lowd_stream_rederive(h, L64);
+        if (r != LOWD_OK) { dfree(&L64); return r; }
+    } else if (h->m_pad > 0) {
+        LOWD_LAUNCH(k_rederive, grid_for(h->m_pad), kT, 0, st, h->m_pad, h->cuv, h->cw, h->cs, L64);
+    }
     LOWD_LAUNCH(k_load_stats, grid_for(h->n), kT, 0, st, L64, h->n, h->l, h->l_lo, h->d_stats);
     double tmp3[3];
     cudaError_t e = cudaGetLastError();
@@ -887,8 +893,10 @@ lowd_status lowd_sweep_run(lowd_ctx* h, int32_t k, const lowd_options* opt, lowd
         LOWD_CK(run_passes(h, step));
         LOWD_CK(cudaMemcpyAsync(h->h_pin + 8, h->d_i32 + 8, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
         LOWD_CK(cudaStreamSynchronize(h->st));
-        if (*(int32_t*)(h->h_pin + 8) != 0) {
-            snprintf(h->err, sizeof(h->err), "sweep: a bounded wait on a staged copy expired");
+        const int32_t kerr = *(int32_t*)(h->h_pin + 8);
+        if (kerr != 0) {
+            snprintf(h->err, sizeof(h->err), "%s", (kerr & 4) ? "sweep: a read descriptor pointed outside the stages"
+                                                               : "sweep: a bounded wait on a staged copy expired");
             return LOWD_ERR_CUDA;
         }
         done += step;

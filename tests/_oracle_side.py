@@ -16,11 +16,12 @@ def oracle_graph(orc, g, prune):
     return orc.compact(g.n, u, v, w, keep)
 
 
-def assert_same_schedule(orc, n, u, v, perm, offs):
-    """The GPU's pass order (perm, class offsets) must visit the oracle's circle-colouring
-    classes, as sets, in the same order (empty colours skipped); the order inside a class
-    is free.  Returns the oracle's own order, which the oracle then replays."""
-    order, _, colour = orc.circle_order(n, u, v)
+def assert_same_schedule(orc, n, u, v, perm, offs, level=False):
+    """The GPU's pass order (perm, class offsets) must visit the oracle's colour classes (the
+    circle colouring, or with level=True the level order of the streamed schedule), as sets,
+    in the same order (empty colours skipped); the order inside a class is free.  Returns the
+    oracle's own order, which the oracle then replays."""
+    order, _, colour = (orc.level_order if level else orc.circle_order)(n, u, v)
     perm = np.asarray(perm)
     offs = np.asarray(offs)
     m = np.asarray(u).shape[0]

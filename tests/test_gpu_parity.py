@@ -363,13 +363,22 @@ def test_edge_cases(pkg, orc):
     pkg.lowd_free(h)
 
 
-def test_too_large_for_shared_memory_sweep_is_an_error(pkg):
+def test_too_large_for_shared_memory_takes_the_stream_schedule(pkg):
+    """60,000 nodes do not fit the one-CTA sweep: asking for it is an error, the automatic
+    choice is the streamed schedule (a perfect matching: one class, every load 1/2)."""
     g = synth.Graph(n=60000, u=np.arange(0, 59998, 2, dtype=np.int32),
                     v=np.arange(1, 59999, 2, dtype=np.int32), w=None)
     h = _load(pkg, g, True)
     with pytest.raises(pkg.LowdError) as e:
-        pkg.lowd_iterate(h, 1)
+        pkg.lowd_iterate(h, 1, schedule=1)
     assert e.value.status == pkg.LOWD_ERR_TOO_LARGE
+    pkg.lowd_free(h)
+    h = _load(pkg, g, True)
+    pkg.lowd_iterate(h, 3)
+    info = pkg.lowd_get_info(h)
+    assert info["schedule"] == 2 and info["classes"] == 1 and info["sweep_kernel"] == 4
+    lg = _np(pkg.lowd_get_loads(h))
+    assert np.all(lg[:59998] == 0.5) and np.all(lg[59998:] == 0.0)
     pkg.lowd_free(h)
 
 
