@@ -78,15 +78,56 @@ def _unkey(k: np.ndarray):
             (k & np.uint64(0xFFFFFFFF)).astype(np.int32))
 
 
+def _first_index(keys: np.ndarray) -> np.ndarray:
+    """Index of the first occurrence of every distinct key (in ascending key order).
+
+    Large arrays are split by the key's top bits into buckets that are deduplicated in
+    parallel threads (numpy's sort releases the GIL); the result is the same set of first
+    indices as one np.unique(keys, return_index=True)."""
+    if keys.shape[0] < (1 << 22):
+        return np.unique(keys, return_index=True)[1]
+    import concurrent.futures as cf
+    import os
+    top = int(keys.max()).bit_length()
+    shift = np.uint64(max(top - 6, 0))
+    bucket = (keys >> shift).astype(np.uint8)            # at most 64 buckets
+    idx = np.argsort(bucket, kind="stable")               # a stable radix sort on uint8
+    counts = np.bincount(bucket, minlength=64)
+    bounds = np.concatenate([[0], np.cumsum(counts)])
+
+    def one(b):
+        ids = idx[bounds[b]:bounds[b + 1]]               # ascending positions
+        if ids.shape[0] == 0:
+            return ids
+        return ids[np.unique(keys[ids], return_index=True)[1]]
+
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        parts = list(ex.map(one, range(64)))
+    return np.concatenate(parts)
+
+
 def _first_unique(keys: np.ndarray, target: int | None):
     """Unique keys in order of first occurrence, cut to ``target`` if given."""
-    uniq, first = np.unique(keys, return_index=True)
-    if target is not None and uniq.shape[0] < target:
+    first = _first_index(keys)
+    if target is not None and first.shape[0] < target:
         return None
     order = np.sort(first)
     if target is not None:
         order = order[:target]
     return keys[order]
+
+
+def _union_sorted(keys: np.ndarray, extra: np.ndarray) -> np.ndarray:
+    """Sorted union of two arrays of distinct keys (np.union1d's result, by sort and merge)."""
+    ks = np.sort(keys)
+    ex = np.unique(extra)
+    if ks.shape[0] and ex.shape[0]:
+        pos = np.minimum(np.searchsorted(ks, ex), ks.shape[0] - 1)
+        ex = ex[ks[pos] != ex]
+    out = np.concatenate([ks, ex])
+    out.sort()
+    return out
 
 
 def _add_block(rng, n: int, keys: np.ndarray, size: int, p: float):
@@ -98,7 +139,7 @@ def _add_block(rng, n: int, keys: np.ndarray, size: int, p: float):
     iu, ju = np.triu_indices(size, k=1)
     keep = rng.random(iu.shape[0]) < p
     bkeys = _keys(nodes[iu[keep]], nodes[ju[keep]])
-    return np.union1d(keys, bkeys), nodes.astype(np.int32), bkeys
+    return _union_sorted(keys, bkeys), nodes.astype(np.int32), bkeys
 
 
 def _finish(n, keys, w_of_key=None, block=None, name=""):

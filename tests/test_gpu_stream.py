@@ -123,13 +123,15 @@ def test_stream_schedule_converges_to_the_exact_loads(pkg, orc):
 
 @pytest.mark.parametrize("n,m,weighted", [(8000, 40000, True), (60000, 240000, False)])
 def test_stream_schedule_finds_the_densest_subgraph(pkg, orc, n, m, weighted):
-    """Until the certified gap (D - rho(S))/rho(S) <= 1e-9: S* = B_1 and rho* exact (the
-    60,000-node graph takes the schedule automatically)."""
+    """Until the certified gap (D - rho(S))/rho(S) <= 1e-6 (the FP32 splits round by
+    2^-24 w_e, so far smaller gaps are not certifiable from them): S* = B_1 and rho* exact
+    (the 60,000-node graph takes the schedule automatically)."""
     g = synth.chung_lu(n, m, 2.2, seed=17, block_size=60, block_p=0.5)
     w = synth.quantise_weights(np.random.default_rng(10).lognormal(0, 1, g.m)) if weighted else None
     h = _load(pkg, g, w)
-    st = pkg.lowd_iterate(h, 8000, check_every=50, rel_tol=1e-9, schedule=2 if n < 53248 else 0)
+    st = pkg.lowd_iterate(h, 8000, check_every=50, rel_tol=1e-6, schedule=2 if n < 53248 else 0)
     assert st["converged"] == 1
+    assert (st["max_load"] - st["rho_best"]) / st["rho_best"] <= 1e-6
     assert pkg.lowd_get_info(h)["sweep_kernel"] == 4
     S, rho, _ = pkg.lowd_extract(h)
     wu, scale = orc.weight_units(g.m, None if w is None else w.astype(np.float64))
