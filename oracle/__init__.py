@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lowd_oracle.c")
+_SRC_THREADS = os.path.join(_HERE, "lowd_threads.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liblowd_oracle.so")
 WEIGHT_SCALE = 1 << 20   # weighted graphs: integer units of 2^-20
@@ -31,9 +32,11 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C, -O2, no target-specific flags)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_THREADS))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC,
+                               _SRC_THREADS, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -62,6 +65,8 @@ def _load():
         lib.orc_ldd.restype = i32
         lib.orc_ldd.argtypes = [i32, i64, P, P, P, P, P, P]
         lib.orc_load_stats.argtypes = [i32, P, P]
+        lib.orc_lowd_iterate_threads.restype = i32
+        lib.orc_lowd_iterate_threads.argtypes = [i32, i64, P, P, P, P, i32, i32, i32, P, P, P]
         lib.orc_level_colouring.restype = i32
         lib.orc_level_colouring.argtypes = [i32, i64, P, P, P]
         _lib = lib
@@ -199,6 +204,23 @@ class LowdState:
                              _p(self.fu), _p(self.fv), _p(self.l), _p(ss))
         self.iters += T
         return ss[:T] if record_sumsq else None
+
+    def iterate_threads(self, T: int, order, class_offsets, threads: int):
+        """T passes in ``order`` on ``threads`` host threads, one class at a time: the edges
+        of class c are order[class_offsets[c]:class_offsets[c + 1]] and must form a matching
+        (no two share a node), so the result equals iterate(T, order) exactly.  Used to time
+        the oracle on all host cores (lowd_threads.c)."""
+        lib = _load()
+        od = _c(order, np.int32)
+        off = _c(class_offsets, np.int64)
+        if od.shape[0] != self.m or off[-1] != self.m:
+            raise ValueError("order and class offsets must cover every edge once")
+        r = lib.orc_lowd_iterate_threads(self.n, self.m, _p(self.u), _p(self.v), _p(od), _p(off),
+                                         int(off.shape[0] - 1), int(T), int(threads),
+                                         _p(self.fu), _p(self.fv), _p(self.l))
+        if r != 0:
+            raise RuntimeError("could not start the threads")
+        self.iters += T
 
     def stats(self):
         """(sum l, sum l^2, max l)."""

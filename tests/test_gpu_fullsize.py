@@ -87,3 +87,28 @@ def test_rmat22_prune_core_and_passes(setup):
     assert np.array_equal(S.cpu().numpy(), idmap[So])
     assert rho == Wo / So.shape[0]
     pkg.lowd_free(h)
+
+
+def test_rmat22_unpruned_streamed_pass(setup):
+    """Algorithm 1 over the whole unpruned graph (the throughput definition for this
+    workload): 4.19 M nodes take the streamed schedule automatically, its classes are the
+    oracle's level order (exactly Delta of them), and one pass agrees with the oracle's FP64
+    replay of that order within the pair-load bar."""
+    torch, pkg, orc, g = setup
+    h = pkg.lowd_load_graph(g.n, torch.from_numpy(g.u).cuda(), torch.from_numpy(g.v).cuda())
+    pkg.lowd_iterate(h, 1)
+    info = pkg.lowd_get_info(h)
+    assert info["schedule"] == 2 and info["sweep_kernel"] == 4
+    deg = np.bincount(g.u, minlength=g.n) + np.bincount(g.v, minlength=g.n)
+    assert info["classes"] >= deg.max()
+    perm, offs = (x.cpu().numpy() for x in pkg.lowd_get_edge_order(h))
+    order = assert_same_schedule(orc, g.n, g.u, g.v, perm, offs, level=True)
+    o = orc.LowdState(g.n, g.u, g.v)
+    o.iterate(1, order=order)
+    lg = pkg.lowd_get_loads(h).cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(lg - o.l)) <= LOAD_TOL * o.l.max()
+    st = pkg.lowd_iterate(h, 0)
+    assert abs(st["sum_load"] - g.m) <= 1e-9 * g.m
+    s = pkg.lowd_get_splits(h).cpu().numpy()
+    assert np.all(s >= 0) and np.all(s <= 1)
+    pkg.lowd_free(h)

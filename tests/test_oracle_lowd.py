@@ -155,3 +155,18 @@ def test_order_within_a_matching_does_not_matter(oracle_mod):
     assert np.array_equal(s1.l, s2.l) and np.array_equal(s1.fu, s2.fu)
     s3 = oracle_mod.LowdState(g.n, g.u, g.v); s3.iterate(20)
     assert not np.array_equal(s1.l, s3.l)      # a different order gives other iterates
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_threaded_passes_equal_the_sequential_passes(oracle_mod, threads):
+    """The all-cores timing variant (classes split over threads, a barrier per class) gives
+    exactly the sequential oracle's state in the same order: the classes are matchings."""
+    import synth
+    g = synth.chung_lu(3000, 20000, 2.2, seed=31, block_size=30, block_p=0.5)
+    w = synth.quantise_weights(np.random.default_rng(8).lognormal(0, 1, g.m)).astype(np.float64)
+    for order, offs, _ in (oracle_mod.circle_order(g.n, g.u, g.v), oracle_mod.level_order(g.n, g.u, g.v)):
+        a = oracle_mod.LowdState(g.n, g.u, g.v, w)
+        b = oracle_mod.LowdState(g.n, g.u, g.v, w)
+        a.iterate(6, order=order)
+        b.iterate_threads(6, order, offs, threads)
+        assert np.array_equal(a.l, b.l) and np.array_equal(a.fu, b.fu) and np.array_equal(a.fv, b.fv)
