@@ -308,10 +308,10 @@ def leg_unpruned(torch, pkg, stream, g, du, dv, dw, T, peak, peak_kind):
     b.record(stream)
     b.synchronize()
     prep_ms = a.elapsed_time(b)
-    info = pkg.lowd_get_info(h)
     st0 = pkg.lowd_iterate(h, 0)
     sec = sweep_launch_seconds(torch, pkg, stream, h, T)
     st1 = pkg.lowd_iterate(h, 0)
+    info = pkg.lowd_get_info(h)
     bpu = BYTES_PER_UPDATE + (4 if g.w is not None else 0)
     achieved = bpu * g.m * T / sec / 1e9
     C = info["classes"]

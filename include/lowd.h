@@ -76,6 +76,10 @@ typedef struct {
     int32_t rederive_every; /* re-derive the FP32 loads from the splits (FP64 sums) after at
                              most this many passes, bounding the drift of the running FP32
                              loads: 0 = default 50, < 0 = only at the end of the call */
+    int32_t class_barriers; /* 1: the one-CTA staged sweep synchronises all its threads after
+                             every colour class (kernel 1) even where the variant that waits
+                             only for the previous updates of each edge's two nodes (kernel 5)
+                             applies; both give the same pass.  Default 0 */
 } lowd_options;
 
 /* Statistics of the state after lowd_iterate (FP64, from loads re-derived from the
@@ -105,8 +109,10 @@ typedef struct {
     int32_t max_degree;   /* maximum (unweighted) degree of the current graph */
     int32_t prune_rounds; /* rounds lowd_prune ran */
     int32_t sweep_kernel; /* kernel of the last pass: 0 none yet, 1 staged one-CTA sweep with
-                             pair loads, 2 one-CTA register-ring sweep, 3 one-CTA simple
-                             sweep, 4 streamed sweep (schedule 2, loads in global memory) */
+                             pair loads and a barrier per class, 2 one-CTA register-ring sweep,
+                             3 one-CTA simple sweep, 4 streamed sweep (schedule 2, loads in
+                             global memory), 5 staged one-CTA sweep with pair loads and
+                             per-node versions instead of class barriers */
     int32_t sweep_edges_per_thread; /* edges per consumer thread per class of kernel 1 */
 } lowd_info;
 

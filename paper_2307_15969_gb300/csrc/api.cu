@@ -44,7 +44,7 @@ lowd_status to_caller(lowd_ctx* h, T* dst, const T* src_dev, size_t n) {
 void free_all(lowd_ctx* h) {
     dfree(&h->u); dfree(&h->v); dfree(&h->w); dfree(&h->wu); dfree(&h->map);
     dfree(&h->sort_perm); dfree(&h->removal_round);
-    dfree(&h->perm); dfree(&h->coff); dfree(&h->coff_real); dfree(&h->cuv);
+    dfree(&h->perm); dfree(&h->coff); dfree(&h->coff_real); dfree(&h->cuv); dfree(&h->crk);
     dfree(&h->cw); dfree(&h->cs); dfree(&h->l); dfree(&h->l_lo);
     dfree(&h->s2_ctab); dfree(&h->s2_beg); dfree(&h->s2_ea); dfree(&h->s2_eb);
     dfree(&h->s2_srcA); dfree(&h->s2_srcB); dfree(&h->s2_lp);
@@ -205,8 +205,10 @@ lowd_status lowd_prune(lowd_handle h, int32_t* n_kept, int64_t* m_kept, int32_t*
 lowd_status lowd_iterate(lowd_handle h, int32_t k, const lowd_options* opt, lowd_stats* st) {
     LOWD_TRY(check_handle(h));
     if (k < 0) return LOWD_ERR_INVALID_ARG;
-    if (opt && (opt->check_every < 0 || opt->rel_tol < 0 || opt->schedule < 0 || opt->schedule > 2))
+    if (opt && (opt->check_every < 0 || opt->rel_tol < 0 || opt->schedule < 0 || opt->schedule > 2 ||
+                opt->class_barriers < 0 || opt->class_barriers > 1))
         return LOWD_ERR_INVALID_ARG;
+    h->no_flow = opt ? opt->class_barriers : 0;
     if (!h->inited) LOWD_TRY(lowd_sweep_prepare(h, opt ? opt->schedule : 0, nullptr));
     return lowd_sweep_run(h, k, opt, st);
 }

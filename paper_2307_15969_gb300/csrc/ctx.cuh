@@ -58,6 +58,9 @@ struct lowd_ctx {
     int32_t* coff_real = nullptr; // [C+1] class offsets without padding
     int32_t* coff_h = nullptr; // [C+1] host copy of coff
     uint32_t* cuv = nullptr;   // [m_pad] packed ends (lo | hi << 16); padding: (n | n << 16)
+    uint32_t* crk = nullptr;   // [m_pad] rank of each end among its node's updates per pass
+                               // (16 bits per end, bit 15 = the node's last update)
+    int no_flow = 0;           // 1: the staged sweep keeps its class barriers (kernel 1)
     float* cw = nullptr;       // [m_pad] weights (weighted only); padding 0
     float* cs = nullptr;       // [m_pad] splits f_e(lo); padding 0
     float* l = nullptr;        // [n + 1] loads; slot n is the padding sentinel

@@ -234,6 +234,7 @@ constexpr int kHdrInts = 20;        // chunk header: begin, padded size, segment
 constexpr int kConsumers = 512;
 constexpr int kProducerWarps = 2;
 constexpr int kStoreGroups = 8;
+constexpr int kLead = 3;            // D: chunks gathered ahead of the consumers; S = 2D stages
 
 struct StreamLayout {
     uint32_t E;          // edges per stage (multiple of 4)
@@ -552,8 +553,8 @@ k_sweep_stream(int32_t n, int32_t NC, const int32_t* __restrict__ ctab, const in
         };
         auto wait_bar = [&](uint64_t* bar, uint32_t par) -> bool {   // producer thread 0 only
             uint32_t spins = 0;
-            bool ok = mbar_try_wait_sleep(bar, par, 1000);
-            while (!ok && !abort_flag && ++spins < kSpinLimit) ok = mbar_try_wait_sleep(bar, par, 1000);
+            bool ok = mbar_try_wait(bar, par);
+            while (!ok && !abort_flag && ++spins < kSpinLimit) ok = mbar_try_wait(bar, par);
             return ok;
         };
         // chunk ranges, fetched one step ahead of their meta copy
@@ -590,8 +591,9 @@ k_sweep_stream(int32_t n, int32_t NC, const int32_t* __restrict__ ctab, const in
                 // store must have finished reading it, and every store older than the last
                 // kStoreGroups must be complete (a chunk's splits are read again a pass later)
                 if (pt == 0) {
+                    // the stage's last split store was committed D - 1 iterations ago
                     bulk_wait<kStoreGroups>();
-                    bulk_wait_read<0>();
+                    bulk_wait_read<kLead - 1>();
                 }
                 fence_proxy_async_smem();   // generic reads of the stage before async writes
                 producer_sync();
@@ -802,7 +804,7 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
         std::vector<int32_t> coff((size_t)C + 1, 0);
         if (cudaMemcpyAsync(coff.data(), h->coff_real, sizeof(int32_t) * ((size_t)C + 1), cudaMemcpyDeviceToHost, st) !=
                 cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
-        const int32_t D = 3, S = 2 * D;
+        const int32_t D = kLead, S = 2 * kLead;
         const size_t budget = 227 * 1024 - kRingHead - 1024;
         const uint32_t E = stream_edges_per_stage(S, weighted, budget);
         // header rows: [0] padded begin, [1] padded size, [2] segments, [3 + g] end of segment

@@ -596,6 +596,237 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
     }
 }
 
+// ------------------------------------------------------------------ staged sweep without class barriers
+//
+// The same staging as k_sweep_tma, but consumers do not meet at a barrier after every class.
+// Instead every node carries a version in shared memory: the number of its updates done in
+// the current pass (bit 15 holds the pass parity).  Each edge end carries its rank among
+// its node's updates in the pass order (bit 15: the last one).  An update waits until both
+// of its nodes show the version equal to its ranks, updates, then publishes rank + 1 (or
+// the next pass's parity after the node's last update).  Every update therefore sees the
+// loads left by the updates before it at its two nodes - the sequential pass in class
+// order - while warps run ahead into later classes wherever those updates are done: a core
+// node takes part in a fraction of the classes only, so most waits are already satisfied.
+
+constexpr uint32_t kFlowSpins = 1u << 22;   // bounded wait on a version
+
+__device__ __forceinline__ void fence_cta() { asm volatile("fence.acq_rel.cta;" ::: "memory"); }
+
+struct FlowLayout {
+    uint32_t bars, L, V, CO, stages, stage_bytes, arr_bytes, total;
+};
+
+__host__ __device__ inline FlowLayout flow_layout(int32_t n, int32_t C, int32_t S, int32_t Emax, bool weighted,
+                                                  int32_t G) {
+    FlowLayout t;
+    t.bars = 0;
+    t.L = 16u * kTmaMaxStages;                       // S full + S empty mbarriers
+    t.V = t.L + 8u * (uint32_t)(n + 1);
+    t.CO = (t.V + 4u * (uint32_t)(n + 1) + 15u) & ~15u;
+    const uint32_t NC = (uint32_t)((C + G - 1) / G);
+    const uint32_t end = t.CO + 4u * (NC + 1u);
+    t.stages = (end + 127u) & ~127u;
+    t.arr_bytes = ((4u * (uint32_t)Emax) + 127u) & ~127u;
+    t.stage_bytes = t.arr_bytes * (weighted ? 4u : 3u);   // ends, splits, ranks (, weights)
+    t.total = t.stages + t.stage_bytes * (uint32_t)S;
+    return t;
+}
+
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(kTmaConsumers + 32, 1)
+k_sweep_flow(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32_t* __restrict__ cuv,
+             const uint32_t* __restrict__ crk, const float* __restrict__ cw, float* __restrict__ cs,
+             float* __restrict__ l, float* __restrict__ l_lo, int32_t passes, int32_t S, int32_t G, int32_t Emax,
+             int32_t* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const FlowLayout lay = flow_layout(n, C, S, Emax, WEIGHTED, G);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bars);
+    uint64_t* empty = full + S;
+    float2* L = reinterpret_cast<float2*>(smem + lay.L);
+    volatile uint32_t* V = reinterpret_cast<volatile uint32_t*>(smem + lay.V);
+    int32_t* CK = reinterpret_cast<int32_t*>(smem + lay.CO);
+    unsigned char* stages = smem + lay.stages;
+    __shared__ volatile int32_t abort_flag;
+    const int tid = threadIdx.x;
+    const int nc = blockDim.x - 32;
+    const int nwarps = nc >> 5;
+    const int32_t NC = (C + G - 1) / G;
+    for (int i = tid; i <= n; i += blockDim.x) {
+        L[i] = i < n ? make_float2(l[i], l_lo[i]) : make_float2(0.0f, 0.0f);
+        V[i] = 0u;
+    }
+    for (int i = tid; i <= NC; i += blockDim.x) CK[i] = coff[min(i * G, C)];
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], nwarps);   // every consumer warp releases the stage
+        }
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    const int32_t P = NC * passes;           // the launcher keeps this < 2^31
+    const int32_t ahead = S - kStoreSlack;
+    if (tid >= nc) {
+        // ---------------- producer warp (lane 0 works): as in k_sweep_tma, plus the ranks
+        if (tid == nc) {
+            int32_t pf = 0, kf = 0, jf = 0;
+            auto fill = [&]() {
+                const int32_t beg = CK[jf];
+                const int32_t end = CK[jf + 1];
+                const uint32_t bytes = 4u * (uint32_t)(end - beg);
+                unsigned char* st = stages + lay.stage_bytes * (uint32_t)kf;
+                mbar_expect_tx(&full[kf], bytes * (WEIGHTED ? 4u : 3u));
+                bulk_g2s(st, cuv + beg, bytes, &full[kf]);
+                bulk_g2s(st + lay.arr_bytes, cs + beg, bytes, &full[kf]);
+                bulk_g2s(st + 2 * lay.arr_bytes, crk + beg, bytes, &full[kf]);
+                if (WEIGHTED) bulk_g2s(st + 3 * lay.arr_bytes, cw + beg, bytes, &full[kf]);
+                ++pf;
+                kf = (kf + 1 == S) ? 0 : kf + 1;
+                jf = (jf + 1 == NC) ? 0 : jf + 1;
+            };
+            while (pf < ahead && pf < P) fill();
+            int32_t k = 0, j = 0;
+            uint32_t parity = 0;
+            int32_t q = 0;
+            for (; q < P; ++q) {
+                uint32_t spins = 0;
+                bool ok = mbar_try_wait_sleep(&empty[k], parity, 1000);
+                while (!ok && !abort_flag && ++spins < kWaitLimit) ok = mbar_try_wait_sleep(&empty[k], parity, 1000);
+                if (!ok) { abort_flag = 1; break; }
+                const int32_t beg = CK[j];
+                const int32_t end = CK[j + 1];
+                bulk_s2g(cs + beg, stages + lay.stage_bytes * (uint32_t)k + lay.arr_bytes, 4u * (uint32_t)(end - beg));
+                bulk_commit();
+                if (pf < P) {
+                    bulk_wait<kStoreGroups>();
+                    bulk_wait_read<kStoreSlack>();
+                    fill();
+                }
+                if (++k == S) { k = 0; parity ^= 1u; }
+                j = (j + 1 == NC) ? 0 : j + 1;
+            }
+            if (q < P) drain_fills(full, S, q, pf, kWaitLimit);
+            bulk_wait<0>();
+            if (abort_flag) atomicOr(err, 1);
+        }
+        return;
+    }
+    // ---------------- consumers: each warp walks the chunks on its own
+    const int lane = tid & 31;
+    auto class_offsets = [&](int32_t jc) -> int32_t {
+        const int32_t c = jc * G + lane;
+        return (lane <= G && c <= C) ? __ldg(coff + c) : 0;
+    };
+    int32_t off_cur = class_offsets(0);
+    int32_t off_nxt = class_offsets(NC > 1 ? 1 : 0);
+    int32_t k = 0, j = 0;
+    uint32_t parity = 0;
+    bool bad = false;
+    for (int32_t q = 0; q < P; ++q) {
+        // stage of chunk q landed? (lane 0 waits; the warp synchronises on the answer)
+        bool ok = true;
+        if (lane == 0) {
+            uint32_t spins = 0;
+            ok = mbar_try_wait(&full[k], parity);
+            while (!ok && !abort_flag && ++spins < kWaitLimit) ok = mbar_try_wait(&full[k], parity);
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) { bad = true; break; }
+        const uint32_t tb = (uint32_t)((q / NC) & 1) << 15;   // pass parity
+        const int32_t c0 = j * G;
+        const int32_t c1 = min(c0 + G, C);
+        const int32_t base = __shfl_sync(0xffffffffu, off_cur, 0);
+        unsigned char* st = stages + lay.stage_bytes * (uint32_t)k;
+        const uint32_t* suv = reinterpret_cast<const uint32_t*>(st);
+        float* ss = reinterpret_cast<float*>(st + lay.arr_bytes);
+        const uint32_t* srk = reinterpret_cast<const uint32_t*>(st + 2 * lay.arr_bytes);
+        const float* sw = reinterpret_cast<const float*>(st + 3 * lay.arr_bytes);
+        int32_t cb = 0;
+        for (int32_t c = c0; c < c1; ++c) {
+            const int32_t ce = __shfl_sync(0xffffffffu, off_cur, c - c0 + 1) - base;
+            const int32_t r = cb + tid;
+            if (r < ce && !bad) {
+                const uint32_t uv = suv[r];
+                const uint32_t a = end_a(uv), b = end_b(uv);
+                if ((int32_t)a < n) {   // padding edges join the sentinel n to itself
+                    const uint32_t rk = srk[r];
+                    const uint32_t ea = tb | (rk & 0x7fffu), eb = tb | ((rk >> 16) & 0x7fffu);
+                    uint32_t spins = 0;
+                    while (V[a] != ea || V[b] != eb) {
+                        if (++spins > kFlowSpins || abort_flag) { bad = true; break; }
+                    }
+                    if (!bad) {
+                        fence_cta();   // acquire: the loads below after the versions seen
+                        float2 A = L[a], B = L[b];
+                        const float sv = ss[r];
+                        const float wv = WEIGHTED ? sw[r] : 1.0f;
+                        const float ns = comp_transfer(A, B, sv, wv);
+                        L[a] = A;
+                        L[b] = B;
+                        ss[r] = ns;
+                        fence_cta();   // release: the loads above before the versions
+                        V[a] = (rk & 0x8000u) ? (tb ^ 0x8000u) : ea + 1u;
+                        V[b] = (rk & 0x80000000u) ? (tb ^ 0x8000u) : eb + 1u;
+                    }
+                }
+            }
+            cb = ce;
+        }
+        fence_proxy_async_smem();   // this warp's split writes before the bulk store reads them
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[k]);
+        if (++k == S) { k = 0; parity ^= 1u; }
+        j = (j + 1 == NC) ? 0 : j + 1;
+        off_cur = off_nxt;
+        off_nxt = class_offsets(j + 1 == NC ? 0 : j + 1);
+        if (__any_sync(0xffffffffu, bad)) { bad = true; break; }
+    }
+    if (bad) {
+        abort_flag = 1;
+        if (lane == 0) atomicOr(err, 1);
+    }
+    // every warp must have released every stage before the loads are written back
+    asm volatile("bar.sync 1, %0;" ::"r"(nc) : "memory");
+    for (int i = tid; i < n; i += nc) {
+        const float2 x = L[i];
+        const float u = x.x + x.y;
+        l[i] = u;
+        l_lo[i] = x.y - (u - x.x);
+    }
+}
+
+// rank of every end among its node's updates in the pass order (bit 15: the last one)
+__global__ void k_occurrence_keys(const uint32_t* __restrict__ cuv, int64_t m_pad, uint32_t* __restrict__ key,
+                                  int32_t* __restrict__ val) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m_pad;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t uv = cuv[p];
+        key[2 * p] = uv & 0xffffu;
+        key[2 * p + 1] = uv >> 16;
+        val[2 * p] = (int32_t)(2 * p);
+        val[2 * p + 1] = (int32_t)(2 * p + 1);
+    }
+}
+
+__global__ void k_occurrence_ranks(const uint32_t* __restrict__ key, const int32_t* __restrict__ val, int64_t N,
+                                   uint32_t n, uint16_t* __restrict__ rk) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = key[j];
+        if (x >= n) continue;   // padding ends
+        // first entry of x: binary search for the first j' with key[j'] == x
+        int64_t lo = 0, hi = j;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (key[mid] < x) lo = mid + 1; else hi = mid;
+        }
+        const bool last = (j + 1 == N) || key[j + 1] != x;
+        rk[val[j]] = (uint16_t)(((j - lo) & 0x7fff) | (last ? 0x8000 : 0));
+    }
+}
+
 // Schedules with fewer classes than the ring depth: same layout, no prefetch ring.
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(kVecThreads, 1)
@@ -670,12 +901,60 @@ cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* 
 }
 
 template <bool WEIGHTED>
+cudaError_t launch_sweep_flow(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* launched) {
+    *launched = false;
+    if (!h->crk || maxlen > kTmaConsumers) return cudaSuccess;
+    const size_t budget = 227 * 1024;
+    constexpr int kMinStages = 3;
+    int32_t G = 0, S = 0, chunk = 0;
+    FlowLayout lay{};
+    for (int32_t g : {16, 8, 4, 2, 1}) {
+        int32_t mx = 0;
+        for (int32_t c0 = 0; c0 < h->C; c0 += g) mx = max(mx, h->coff_h[min(c0 + g, h->C)] - h->coff_h[c0]);
+        int32_t s = kTmaMaxStages;
+        FlowLayout t = flow_layout(h->n, h->C, s, mx, WEIGHTED, g);
+        while (s > kMinStages && t.total > budget) t = flow_layout(h->n, h->C, --s, mx, WEIGHTED, g);
+        if (t.total > budget) continue;
+        const int32_t NC = (h->C + g - 1) / g;
+        if (NC < s - kStoreSlack + kStoreGroups + 1) continue;   // split store ordering, as k_sweep_tma
+        G = g; S = s; chunk = mx; lay = t;
+        break;
+    }
+    if (G == 0) return cudaSuccess;
+    const int32_t NC = (h->C + G - 1) / G;
+    int threads = ((maxlen + 31) / 32) * 32;
+    if (threads < 64) threads = 64;
+    auto kern = k_sweep_flow<WEIGHTED>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
+    if (e != cudaSuccess) return e;
+    h->sweep_kernel = 5;
+    h->sweep_E = 1;
+    // the pass parity lives in bit 15 of a version: any number of passes per launch works; the
+    // stream position stays below 2^31
+    const int32_t per = (int32_t)(0x7fffffff / NC);
+    for (int32_t done = 0; done < passes && e == cudaSuccess;) {
+        const int32_t k = passes - done < per ? passes - done : per;
+        LOWD_LAUNCH(kern, 1, threads + 32, lay.total, h->st, h->n, h->C, h->coff, h->cuv, h->crk, h->cw, h->cs,
+                    h->l, h->l_lo, k, S, G, chunk, h->d_i32 + 8);
+        e = cudaGetLastError();
+        done += k;
+    }
+    *launched = true;
+    return e;
+}
+
+template <bool WEIGHTED>
 cudaError_t launch_sweep(lowd_ctx* h, int32_t passes) {
     {
         int32_t maxlen = 0;
         for (int32_t c = 0; c < h->C; ++c) maxlen = max(maxlen, h->coff_h[c + 1] - h->coff_h[c]);
         bool launched = false;
-        cudaError_t e = launch_sweep_tma<WEIGHTED>(h, passes, maxlen, &launched);
+        cudaError_t e = cudaSuccess;
+        if (!h->no_flow) {
+            e = launch_sweep_flow<WEIGHTED>(h, passes, maxlen, &launched);
+            if (e != cudaSuccess || launched) return e;
+        }
+        e = launch_sweep_tma<WEIGHTED>(h, passes, maxlen, &launched);
         if (e != cudaSuccess || launched) return e;
     }
     const size_t lbytes = sizeof(float) * ((size_t)h->n + 1);
@@ -806,6 +1085,29 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
         if (m_pad > 0)
             LOWD_LAUNCH(k_gather_streams, grid_for(m_pad), kT, 0, st, h->perm, m_pad, n, h->u, h->v, h->w,
                         init_splits_canon, h->cuv, h->cw, h->cs);
+        // ranks of every end among its node's updates in the pass order (the staged sweep
+        // without class barriers); node degrees must fit 15 bits
+        if (m_pad > 0 && h->max_deg < 0x7fff) {
+            uint32_t* ok[2] = {nullptr, nullptr};
+            int32_t* ov[2] = {nullptr, nullptr};
+            bool good = (s = h->need_tmp(lowd_sort_tmp_bytes(2 * m_pad))) == LOWD_OK;
+            good = good && (s = dalloc(h, &ok[0], 2 * m_pad)) == LOWD_OK;
+            good = good && (s = dalloc(h, &ok[1], 2 * m_pad)) == LOWD_OK;
+            good = good && (s = dalloc(h, &ov[0], 2 * m_pad)) == LOWD_OK;
+            good = good && (s = dalloc(h, &ov[1], 2 * m_pad)) == LOWD_OK;
+            good = good && (s = dalloc(h, &h->crk, m_pad)) == LOWD_OK;
+            if (good) {
+                cudaMemsetAsync(h->crk, 0, sizeof(uint32_t) * (size_t)m_pad, st);
+                LOWD_LAUNCH(k_occurrence_keys, grid_for(m_pad), kT, 0, st, h->cuv, m_pad, ok[0], ov[0]);
+                const int cur2 = radix_sort_pairs<uint32_t, int32_t>(ok[0], ov[0], ok[1], ov[1], 2 * m_pad,
+                                                                     bit_length_u64((uint64_t)n), h->tmp, st);
+                LOWD_LAUNCH(k_occurrence_ranks, grid_for(2 * m_pad), kT, 0, st, ok[cur2], ov[cur2], 2 * m_pad,
+                            (uint32_t)n, reinterpret_cast<uint16_t*>(h->crk));
+                cudaStreamSynchronize(st);
+            }
+            dfree(&ok[0]); dfree(&ok[1]); dfree(&ov[0]); dfree(&ov[1]);
+            if (!good) break;
+        }
         if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
         h->sched = 1;
         h->inited = 1;

@@ -62,7 +62,7 @@ def test_rmat22_prune_core_and_passes(setup):
     o.iterate(2, order=order)
     lg = pkg.lowd_get_loads(h).cpu().numpy().astype(np.float64)
     info = pkg.lowd_get_info(h)
-    assert info["sweep_kernel"] == 1        # the staged pair-load sweep that bench.py times
+    assert info["sweep_kernel"] in (1, 5)   # the staged pair-load sweep that bench.py times
     assert np.max(np.abs(lg - o.l)) <= LOAD_TOL * o.l.max()
     # properties: conservation, monotone sum of squares, box
     assert abs(st2["sum_load"] - mk) <= 1e-6 * mk

@@ -55,7 +55,7 @@ def test_weighted_rmat_precision_against_fp64(setup, capsys):
     gu, gv, gw = (x.cpu().numpy() for x in pkg.lowd_get_graph(h))
     assert np.array_equal(gu, uh) and np.array_equal(gv, vh) and np.array_equal(gw, wh)
     pkg.lowd_iterate(h, 1)
-    assert pkg.lowd_get_info(h)["sweep_kernel"] == 1      # the staged pair-load sweep, weighted
+    assert pkg.lowd_get_info(h)["sweep_kernel"] in (1, 5)   # the staged pair-load sweep, weighted
     order = assert_same_schedule(orc, nh, uh, vh, *(x.cpu().numpy() for x in pkg.lowd_get_edge_order(h)))
     o = orc.LowdState(nh, uh, vh, wh.astype(np.float64))
     o.iterate(1, order=order)

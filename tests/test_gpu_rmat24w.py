@@ -56,7 +56,7 @@ def test_rmat24w_pruning_and_core_bit_exact(setup):
     assert np.array_equal(gu, uh) and np.array_equal(gv, vh) and np.array_equal(gw, wh)
     # two passes in the oracle's own class order, FP64 replay
     st1 = pkg.lowd_iterate(h, 1)
-    assert pkg.lowd_get_info(h)["sweep_kernel"] == 1
+    assert pkg.lowd_get_info(h)["sweep_kernel"] in (1, 5)
     order = assert_same_schedule(orc, nh, uh, vh, *(x.cpu().numpy() for x in pkg.lowd_get_edge_order(h)))
     st2 = pkg.lowd_iterate(h, 1)
     o = orc.LowdState(nh, uh, vh, wh.astype(np.float64))

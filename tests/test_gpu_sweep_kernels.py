@@ -4,7 +4,9 @@ lowd_iterate picks its pass kernel from the graph's schedule: the staged one-CTA
 pair loads (kernel 1) with one, two or four edges per consumer thread by class size, the
 register-ring sweep (kernel 2) when the staged layout's store ordering does not hold, the
 simple sweep (kernel 3) for very few classes, and the streamed sweep (kernel 4) for graphs
-whose loads do not fit shared memory.  Each case below is sized to reach one variant,
+whose loads do not fit shared memory; kernel 5 is kernel 1 with per-node versions in place of
+the barrier after every class (classes of up to 992 edges).  Each case below is sized to
+reach one variant,
 unit and weighted, and checks lowd_get_info's record of it; the oracle replays its own
 circle-colouring order (checked to be the GPU's classes) in FP64, and the loads must agree
 within the bar of that kernel's arithmetic (Algorithm 1; pair loads 1e-6, single FP32 loads
@@ -39,13 +41,16 @@ def orc():
     return oracle
 
 
-# (graph, passes, expected kernel, expected edges per thread (kernel 1 only))
+# (graph, passes, class barriers forced, expected kernel, expected edges per thread (kernel 1))
 CASES = {
-    "simple_k6": (lambda: synth.small_family("clique", 6), 12, 3, 0),
-    "ring_gnp60": (lambda: synth.erdos_renyi(60, 0.5, seed=61), 20, 2, 0),
-    "staged_e1": (lambda: synth.erdos_renyi(1500, 0.5, seed=62), 6, 1, 1),
-    "staged_e2": (lambda: synth.erdos_renyi(2600, 0.95, seed=63), 4, 1, 2),
-    "staged_e4": (lambda: synth.erdos_renyi(4400, 0.95, seed=64), 3, 1, 4),
+    "simple_k6": (lambda: synth.small_family("clique", 6), 12, False, 3, 0),
+    "ring_gnp60": (lambda: synth.erdos_renyi(60, 0.5, seed=61), 20, False, 2, 0),
+    "versions_e1": (lambda: synth.erdos_renyi(1500, 0.5, seed=62), 6, False, 5, 1),
+    "versions_sparse": (lambda: synth.chung_lu(4000, 30000, 2.3, seed=66, block_size=50, block_p=0.5),
+                        30, False, 5, 1),
+    "staged_e1": (lambda: synth.erdos_renyi(1500, 0.5, seed=62), 6, True, 1, 1),
+    "staged_e2": (lambda: synth.erdos_renyi(2600, 0.95, seed=63), 4, False, 1, 2),
+    "staged_e4": (lambda: synth.erdos_renyi(4400, 0.95, seed=64), 3, False, 1, 4),
 }
 
 
@@ -53,17 +58,17 @@ CASES = {
 @pytest.mark.parametrize("case", list(CASES))
 def test_pass_kernel_variant_against_oracle(pkg, orc, case, weighted):
     import torch
-    make, T, kern, E = CASES[case]
+    make, T, barriers, kern, E = CASES[case]
     g = make()
     w = None
     if weighted:
         w = synth.quantise_weights(np.random.default_rng(len(case)).lognormal(0, 1, g.m))
     h = pkg.lowd_load_graph(g.n, torch.from_numpy(g.u).cuda(), torch.from_numpy(g.v).cuda(),
                             None if w is None else torch.from_numpy(w).cuda())
-    pkg.lowd_iterate(h, T)
+    pkg.lowd_iterate(h, T, class_barriers=barriers)
     info = pkg.lowd_get_info(h)
     assert info["sweep_kernel"] == kern, info
-    if kern == 1:
+    if kern in (1, 5):
         assert info["sweep_edges_per_thread"] == E, info
     perm, offs = (x.cpu().numpy() for x in pkg.lowd_get_edge_order(h))
     order = assert_same_schedule(orc, g.n, g.u, g.v, perm, offs)
