@@ -76,10 +76,11 @@ typedef struct {
     int32_t rederive_every; /* re-derive the FP32 loads from the splits (FP64 sums) after at
                              most this many passes, bounding the drift of the running FP32
                              loads: 0 = default 50, < 0 = only at the end of the call */
-    int32_t class_barriers; /* 1: the one-CTA staged sweep synchronises all its threads after
-                             every colour class (kernel 1) even where the variant that waits
-                             only for the previous updates of each edge's two nodes (kernel 5)
-                             applies; both give the same pass.  Default 0 */
+    int32_t node_versions; /* 1: the one-CTA staged sweep replaces its barrier after every
+                             colour class by per-node versions (kernel 5: an update waits only
+                             for the previous updates of its two nodes); same pass as kernel 1.
+                             Default 0 (kernel 1: on dense cores whose hubs appear in every
+                             class it is faster, as waiting warps sleep at the barrier) */
 } lowd_options;
 
 /* Statistics of the state after lowd_iterate (FP64, from loads re-derived from the

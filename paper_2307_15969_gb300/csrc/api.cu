@@ -206,9 +206,9 @@ lowd_status lowd_iterate(lowd_handle h, int32_t k, const lowd_options* opt, lowd
     LOWD_TRY(check_handle(h));
     if (k < 0) return LOWD_ERR_INVALID_ARG;
     if (opt && (opt->check_every < 0 || opt->rel_tol < 0 || opt->schedule < 0 || opt->schedule > 2 ||
-                opt->class_barriers < 0 || opt->class_barriers > 1))
+                opt->node_versions < 0 || opt->node_versions > 1))
         return LOWD_ERR_INVALID_ARG;
-    h->no_flow = opt ? opt->class_barriers : 0;
+    h->use_versions = opt ? opt->node_versions : 0;
     if (!h->inited) LOWD_TRY(lowd_sweep_prepare(h, opt ? opt->schedule : 0, nullptr));
     return lowd_sweep_run(h, k, opt, st);
 }

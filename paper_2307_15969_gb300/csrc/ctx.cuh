@@ -60,7 +60,7 @@ struct lowd_ctx {
     uint32_t* cuv = nullptr;   // [m_pad] packed ends (lo | hi << 16); padding: (n | n << 16)
     uint32_t* crk = nullptr;   // [m_pad] rank of each end among its node's updates per pass
                                // (16 bits per end, bit 15 = the node's last update)
-    int no_flow = 0;           // 1: the staged sweep keeps its class barriers (kernel 1)
+    int use_versions = 0;      // 1: the staged sweep uses per-node versions (kernel 5)
     float* cw = nullptr;       // [m_pad] weights (weighted only); padding 0
     float* cs = nullptr;       // [m_pad] splits f_e(lo); padding 0
     float* l = nullptr;        // [n + 1] loads; slot n is the padding sentinel
@@ -68,6 +68,8 @@ struct lowd_ctx {
 
     // streamed schedule (2): chunked class-major stream, loads in global memory
     int32_t s2_NC = 0, s2_E = 0, s2_S = 0, s2_D = 0;   // chunks, edges per stage, stages, lead
+    int32_t s2_K = 0;             // leading classes run as grid-wide steps
+    int32_t s2_tail = 0;          // 1 if classes remain for the chunked stream
     int32_t* s2_ctab = nullptr;   // [NC][20] chunk headers
     int32_t* s2_beg = nullptr;    // [NC + 1] padded chunk begins
     int32_t* s2_ea = nullptr;     // [m_pad] ends (node n for padding)

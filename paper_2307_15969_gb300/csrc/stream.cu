@@ -276,10 +276,15 @@ __device__ __host__ inline int32_t chunk_of(const int32_t* beg, int32_t NC, int6
 }
 
 // class-major real position i -> padded position; perm_pad and the streams
-__global__ void k_pad_scatter(const int32_t* __restrict__ order, int64_t m, const int32_t* __restrict__ real_beg,
-                              const int32_t* __restrict__ pad_beg, int32_t NC, int32_t* __restrict__ perm_pad) {
+__global__ void k_pad_scatter(const int32_t* __restrict__ order, int64_t m, int64_t m_grid,
+                              const int32_t* __restrict__ real_beg, const int32_t* __restrict__ pad_beg,
+                              int32_t NC, int32_t* __restrict__ perm_pad) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < m_grid) {   // grid-wide classes keep their positions
+            perm_pad[i] = order[i];
+            continue;
+        }
         const int32_t J = chunk_of(real_beg, NC, i);
         perm_pad[pad_beg[J] + (i - real_beg[J])] = order[i];
     }
@@ -312,13 +317,14 @@ __global__ void k_stream_gather(const int32_t* __restrict__ perm_pad, int64_t m_
     }
 }
 
-// occurrence records (node, 2p + side) in padded-position order; padding sorts last (key n)
+// occurrence records (node, 2p + side) of the chunked positions p >= p0, in position order;
+// padding and the grid-wide part sort last (key n)
 __global__ void k_occurrences(const int32_t* __restrict__ perm_pad, const int32_t* __restrict__ ea,
-                              const int32_t* __restrict__ eb, int64_t m_pad, int32_t n,
+                              const int32_t* __restrict__ eb, int64_t m_pad, int64_t p0, int32_t n,
                               uint32_t* __restrict__ key, int64_t* __restrict__ val) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m_pad;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const bool pad = perm_pad[p] < 0;
+        const bool pad = perm_pad[p] < 0 || p < p0;
         key[2 * p] = pad ? (uint32_t)n : (uint32_t)ea[p];
         key[2 * p + 1] = pad ? (uint32_t)n : (uint32_t)eb[p];
         val[2 * p] = 2 * p;
@@ -685,6 +691,37 @@ k_sweep_stream(int32_t n, int32_t NC, const int32_t* __restrict__ ctab, const in
     }
 }
 
+// The leading classes of the level order are large (on R-MAT, light edges come first: the
+// first few thousand classes hold most edges).  Each of them is one grid-wide step: every
+// thread takes edges of the class, reads both loads from global memory (L2, bypassing L1),
+// updates and writes them back; a grid barrier separates the classes.  The remaining classes
+// (the long tail of small classes around the hubs) go through k_sweep_stream.
+constexpr int kGridThreads = 512;
+constexpr int32_t kGridMinClass = 1024;   // classes at least this large take a grid-wide step
+
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(kGridThreads)
+k_sweep_grid(int32_t K, const int32_t* __restrict__ coff, const int32_t* __restrict__ ea,
+             const int32_t* __restrict__ eb, const float* __restrict__ cw, float* __restrict__ cs,
+             float2* __restrict__ lp, unsigned* __restrict__ bar, int32_t* __restrict__ err) {
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int32_t c = 0; c < K; ++c) {
+        const int32_t b0 = __ldg(coff + c), b1 = __ldg(coff + c + 1);
+        for (int64_t i = b0 + t0; i < b1; i += T) {
+            const int32_t a = __ldg(ea + i), b = __ldg(eb + i);
+            float2 A = __ldcg(lp + a), B = __ldcg(lp + b);
+            const float s = __ldcg(cs + i);
+            const float w = WEIGHTED ? __ldg(cw + i) : 1.0f;
+            const float ns = comp_transfer(A, B, s, w);
+            __stcg(lp + a, A);
+            __stcg(lp + b, B);
+            __stcg(cs + i, ns);
+        }
+        if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host side
@@ -809,8 +846,14 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
         const uint32_t E = stream_edges_per_stage(S, weighted, budget);
         // header rows: [0] padded begin, [1] padded size, [2] segments, [3 + g] end of segment
         // g relative to the begin; real_beg: the chunk's first real (unpadded) position
+        // leading classes of at least kGridMinClass edges take grid-wide steps (positions
+        // [0, coff[K]) of the stream, padded to a multiple of 4); the rest are chunked
+        int32_t K = 0;
+        while (K < C && coff[K + 1] - coff[K] >= kGridMinClass) ++K;
+        const int64_t m_grid = coff[K];
+        const int64_t grid_pad = (m_grid + 3) & ~(int64_t)3;
         std::vector<int32_t> ctab, real_beg;
-        int64_t pad = 0, real = 0;
+        int64_t pad = grid_pad, real = m_grid;
         int32_t cnt = 0, nseg = 0;
         std::vector<int32_t> row(kHdrInts, 0);
         auto open = [&]() {
@@ -828,7 +871,7 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
             pad += padded;
         };
         open();
-        for (int32_t c = 0; c < C; ++c) {
+        for (int32_t c = K; c < C; ++c) {
             int32_t rem = coff[c + 1] - coff[c];
             while (rem > 0) {
                 if (nseg == kSegs || cnt == (int32_t)E) { close(); open(); }
@@ -854,6 +897,8 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
         const int64_t m_pad = pad;
         h->m_pad = m_pad;
         h->s2_NC = NCp;
+        h->s2_K = K;
+        h->s2_tail = real > m_grid ? 1 : 0;
         h->s2_E = (int32_t)E;
         h->s2_S = S;
         h->s2_D = D;
@@ -876,7 +921,7 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
         if ((s = dalloc(h, &h->s2_lp, (size_t)n + 1))) break;
         if (m_pad > 0) {
             LOWD_LAUNCH(k_fill_i32s, grid_for(m_pad), kT, 0, st, h->perm, m_pad, -1);
-            LOWD_LAUNCH(k_pad_scatter, grid_for(m), kT, 0, st, order, m, rb, h->s2_beg, NCp, h->perm);
+            LOWD_LAUNCH(k_pad_scatter, grid_for(m), kT, 0, st, order, m, m_grid, rb, h->s2_beg, NCp, h->perm);
             LOWD_LAUNCH(k_stream_gather, grid_for(m_pad), kT, 0, st, h->perm, m_pad, n, h->u, h->v, h->w,
                         init_splits_canon, h->s2_ea, h->s2_eb, h->cw, h->cs);
             // ---- 7. descriptors from each node's occurrences (sorted by node, stable in position)
@@ -887,7 +932,8 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
             if ((s = dalloc(h, &oval[1], 2 * m_pad))) break;
             if ((s = dalloc(h, &gfirst, n))) break;
             if ((s = dalloc(h, &glast, n))) break;
-            LOWD_LAUNCH(k_occurrences, grid_for(m_pad), kT, 0, st, h->perm, h->s2_ea, h->s2_eb, m_pad, n, okey[0], oval[0]);
+            LOWD_LAUNCH(k_occurrences, grid_for(m_pad), kT, 0, st, h->perm, h->s2_ea, h->s2_eb, m_pad, grid_pad, n,
+                        okey[0], oval[0]);
             const int nb1 = bit_length_u64((uint64_t)n);   // keys 0..n (n = padding)
             int c5 = radix_sort_pairs<uint32_t, int64_t>(okey[0], oval[0], okey[1], oval[1], 2 * m_pad, nb1, h->tmp, st);
             uint32_t* sk = okey[c5];
@@ -928,14 +974,41 @@ cudaError_t lowd_stream_passes(lowd_ctx* h, int32_t passes) {
     h->sweep_kernel = 4;
     h->sweep_E = 0;
     LOWD_LAUNCH(k_pack_loads, grid_for((int64_t)h->n + 1), kT, 0, h->st, h->l, h->l_lo, h->n, h->s2_lp);
-    const int32_t per = (int32_t)(0x7fffffff / h->s2_NC);
-    for (int32_t done = 0; done < passes && e == cudaSuccess;) {
-        const int32_t k = passes - done < per ? passes - done : per;
+    auto stream_launch = [&](int32_t k) {
         LOWD_LAUNCH(kern, 1, kConsumers + kProducerWarps * 32, smem, h->st, h->n, h->s2_NC, h->s2_ctab, h->s2_ea,
                     h->s2_eb, h->s2_srcA, h->s2_srcB, h->cw, h->cs, h->s2_lp, k, h->s2_S, h->s2_D,
                     (uint32_t)h->s2_E, (uint32_t)smem, h->d_i32 + 8);
-        e = cudaGetLastError();
-        done += k;
+        return cudaGetLastError();
+    };
+    cudaMemsetAsync(h->d_i32 + 12, 0, 2 * sizeof(int32_t), h->st);   // grid barrier words
+    if (h->s2_K == 0) {
+        const int32_t per = (int32_t)(0x7fffffff / h->s2_NC);
+        for (int32_t done = 0; done < passes && e == cudaSuccess;) {
+            const int32_t k = passes - done < per ? passes - done : per;
+            e = stream_launch(k);
+            done += k;
+        }
+    } else {
+        // per pass: the large classes as grid-wide steps, then the tail through the stream
+        auto gk = weighted ? k_sweep_grid<true> : k_sweep_grid<false>;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gk, kGridThreads, 0);
+        const int blocks = lowd_device_sms() * (per_sm > 2 ? 2 : (per_sm > 0 ? per_sm : 1));
+        int32_t K = h->s2_K;
+        const int32_t* coff = h->coff_real;
+        const int32_t* pea = h->s2_ea;
+        const int32_t* peb = h->s2_eb;
+        const float* pcw = h->cw;
+        float* pcs = h->cs;
+        float2* plp = h->s2_lp;
+        unsigned* bar = reinterpret_cast<unsigned*>(h->d_i32 + 12);
+        int32_t* errp = h->d_i32 + 8;
+        void* args[] = {&K, &coff, &pea, &peb, &pcw, &pcs, &plp, &bar, &errp};
+        for (int32_t t = 0; t < passes && e == cudaSuccess; ++t) {
+            e = cudaLaunchCooperativeKernel((const void*)gk, dim3(blocks), dim3(kGridThreads), args, 0, h->st);
+            lowd_note_launch();
+            if (e == cudaSuccess && h->s2_tail) e = stream_launch(1);
+        }
     }
     if (e != cudaSuccess) return e;
     LOWD_LAUNCH(k_unpack_loads, grid_for(h->n), kT, 0, h->st, h->s2_lp, h->n, h->l, h->l_lo);

@@ -950,7 +950,7 @@ cudaError_t launch_sweep(lowd_ctx* h, int32_t passes) {
         for (int32_t c = 0; c < h->C; ++c) maxlen = max(maxlen, h->coff_h[c + 1] - h->coff_h[c]);
         bool launched = false;
         cudaError_t e = cudaSuccess;
-        if (!h->no_flow) {
+        if (h->use_versions) {
             e = launch_sweep_flow<WEIGHTED>(h, passes, maxlen, &launched);
             if (e != cudaSuccess || launched) return e;
         }

@@ -41,16 +41,18 @@ def orc():
     return oracle
 
 
-# (graph, passes, class barriers forced, expected kernel, expected edges per thread (kernel 1))
+# (graph, passes, node versions asked for, expected kernel, expected edges per thread
+# (kernels 1 and 5))
 CASES = {
     "simple_k6": (lambda: synth.small_family("clique", 6), 12, False, 3, 0),
     "ring_gnp60": (lambda: synth.erdos_renyi(60, 0.5, seed=61), 20, False, 2, 0),
-    "versions_e1": (lambda: synth.erdos_renyi(1500, 0.5, seed=62), 6, False, 5, 1),
+    "versions_gnp60": (lambda: synth.erdos_renyi(60, 0.5, seed=61), 20, True, 5, 1),
+    "versions_e1": (lambda: synth.erdos_renyi(1500, 0.5, seed=62), 6, True, 5, 1),
     "versions_sparse": (lambda: synth.chung_lu(4000, 30000, 2.3, seed=66, block_size=50, block_p=0.5),
-                        30, False, 5, 1),
-    "staged_e1": (lambda: synth.erdos_renyi(1500, 0.5, seed=62), 6, True, 1, 1),
+                        30, True, 5, 1),
+    "staged_e1": (lambda: synth.erdos_renyi(1500, 0.5, seed=62), 6, False, 1, 1),
     "staged_e2": (lambda: synth.erdos_renyi(2600, 0.95, seed=63), 4, False, 1, 2),
-    "staged_e4": (lambda: synth.erdos_renyi(4400, 0.95, seed=64), 3, False, 1, 4),
+    "staged_e4": (lambda: synth.erdos_renyi(4400, 0.95, seed=64), 3, True, 1, 4),
 }
 
 
@@ -58,14 +60,14 @@ CASES = {
 @pytest.mark.parametrize("case", list(CASES))
 def test_pass_kernel_variant_against_oracle(pkg, orc, case, weighted):
     import torch
-    make, T, barriers, kern, E = CASES[case]
+    make, T, versions, kern, E = CASES[case]
     g = make()
     w = None
     if weighted:
         w = synth.quantise_weights(np.random.default_rng(len(case)).lognormal(0, 1, g.m))
     h = pkg.lowd_load_graph(g.n, torch.from_numpy(g.u).cuda(), torch.from_numpy(g.v).cuda(),
                             None if w is None else torch.from_numpy(w).cuda())
-    pkg.lowd_iterate(h, T, class_barriers=barriers)
+    pkg.lowd_iterate(h, T, node_versions=versions)
     info = pkg.lowd_get_info(h)
     assert info["sweep_kernel"] == kern, info
     if kern in (1, 5):
