@@ -21,8 +21,9 @@ constexpr double kUnit = 1048576.0;  // 2^20 weight units per 1.0
 
 enum { ERR_RANGE = 1, ERR_LOOP = 2, ERR_WEIGHT = 4, ERR_GRID = 8, UNSORTED = 16 };
 
-// One pass over the input pairs: range, loop and weight checks, canonical key
-// lo * n + hi, and whether the input is already strictly increasing in that key.
+// One pass over the input pairs: range, loop and weight checks, and whether the input is
+// already strictly increasing in the canonical key lo * n + hi; with keys != null the keys
+// (and the input position of each) are written for the sort.
 __global__ void k_check_keys(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
                              const float* __restrict__ w, int64_t m, int32_t n,
                              uint64_t* __restrict__ keys, uint32_t* __restrict__ idx,
@@ -31,12 +32,18 @@ __global__ void k_check_keys(const int32_t* __restrict__ u, const int32_t* __res
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         int32_t a = u[e], b = v[e];
-        if (a < 0 || a >= n || b < 0 || b >= n) { flags |= ERR_RANGE; keys[e] = 0; idx[e] = (uint32_t)e; continue; }
+        if (a < 0 || a >= n || b < 0 || b >= n) {
+            flags |= ERR_RANGE;
+            if (keys) { keys[e] = 0; idx[e] = (uint32_t)e; }
+            continue;
+        }
         if (a == b) flags |= ERR_LOOP;
         uint64_t lo = (uint64_t)min(a, b), hi = (uint64_t)max(a, b);
         uint64_t k = lo * (uint64_t)n + hi;
-        keys[e] = k;
-        idx[e] = (uint32_t)e;
+        if (keys) {
+            keys[e] = k;
+            idx[e] = (uint32_t)e;
+        }
         if (w) {
             float x = w[e];
             if (!(x > 0.0f) || !isfinite(x)) flags |= ERR_WEIGHT;
@@ -82,16 +89,53 @@ __global__ void k_emit_unique(const uint64_t* __restrict__ keys, const uint32_t*
     }
 }
 
+// Add the same x to counter[node] for every lane, one atomic per distinct node of the warp
+// (the edge lists are sorted by their low end, so neighbouring lanes often share it).  All
+// lanes of the warp take part; lanes with nothing to add pass node = -1.
+template <class T>
+__device__ __forceinline__ void warp_add(T* counter, int32_t node, T x) {
+    const unsigned peers = __match_any_sync(0xffffffffu, node);
+    if (node >= 0 && (int)lane_id() == __ffs(peers) - 1) atomicAdd(&counter[node], x * (T)__popc(peers));
+}
+
+// Input already strictly increasing in the canonical key: copy it in canonical form.
+__global__ void k_emit_sorted(const int32_t* __restrict__ du, const int32_t* __restrict__ dv,
+                              const float* __restrict__ w_in, int64_t m, int32_t* __restrict__ u,
+                              int32_t* __restrict__ v, float* __restrict__ w, int64_t* __restrict__ wu) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = du[e], b = dv[e];
+        u[e] = min(a, b);
+        v[e] = max(a, b);
+        if (w_in) {
+            const float x = w_in[e];
+            w[e] = x;
+            const double y = rint((double)x * kUnit);
+            wu[e] = y < 1.0 ? 1 : (int64_t)y;
+        }
+    }
+}
+
 // Weighted degree in units (unit weights count 1 per edge) and unweighted degree.
 __global__ void k_degrees(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
                           const int64_t* __restrict__ wu, int64_t m,
                           unsigned long long* __restrict__ deg, int32_t* __restrict__ cnt) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int32_t a = u[e], b = v[e];
-        unsigned long long x = wu ? (unsigned long long)wu[e] : 1ull;
-        if (deg) { atomicAdd(&deg[a], x); atomicAdd(&deg[b], x); }
-        if (cnt) { atomicAdd(&cnt[a], 1); atomicAdd(&cnt[b], 1); }
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = base + threadIdx.x;
+        const bool ok = e < m;
+        const int32_t a = ok ? u[e] : -1, b = ok ? v[e] : -1;
+        if (cnt) {
+            warp_add<int32_t>(cnt, a, 1);
+            warp_add<int32_t>(cnt, b, 1);
+        }
+        if (deg) {
+            if (wu) {   // weights differ per edge: one atomic per end
+                if (ok) { atomicAdd(&deg[a], (unsigned long long)wu[e]); atomicAdd(&deg[b], (unsigned long long)wu[e]); }
+            } else {
+                warp_add<unsigned long long>(deg, a, 1ull);
+                warp_add<unsigned long long>(deg, b, 1ull);
+            }
+        }
     }
 }
 
@@ -151,42 +195,60 @@ __global__ void k_prune_mark(const int32_t* __restrict__ act, int64_t nact,
 }
 
 // Round r, edge side: every live edge with an end removed in this round takes its weight
-// off W(H) and off the degree of a surviving end; edges with both ends alive are
-// appended (warp-aggregated) to the next round's edge list.
-__global__ void k_prune_edges(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
-                              const int64_t* __restrict__ ew, int64_t me, int32_t r,
-                              const int32_t* __restrict__ rr, unsigned long long* __restrict__ deg,
-                              unsigned long long* __restrict__ removedW,
-                              int32_t* __restrict__ nu, int32_t* __restrict__ nv,
-                              int64_t* __restrict__ nw, unsigned long long* __restrict__ ncount) {
+// off W(H) and off the degree of a surviving end; edges with both ends alive go to the next
+// round's edge list (in any order: the list only drives the rounds).  A block takes tiles of
+// kPruneTile edges and reserves room for a tile's survivors with one atomic; unit-weight
+// decrements are aggregated per warp on equal nodes.
+constexpr int kPruneItems = 8;
+constexpr int kPruneTile = kT * kPruneItems;
+
+__global__ void __launch_bounds__(kT)
+k_prune_edges(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+              const int64_t* __restrict__ ew, int64_t me, int32_t r,
+              const int32_t* __restrict__ rr, unsigned long long* __restrict__ deg,
+              unsigned long long* __restrict__ removedW,
+              int32_t* __restrict__ nu, int32_t* __restrict__ nv,
+              int64_t* __restrict__ nw, unsigned long long* __restrict__ ncount) {
+    __shared__ unsigned long long sh_base;
+    __shared__ int32_t sh_scan[kT / 32 + 1];
     unsigned long long acc = 0;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < me;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        int64_t e = base + threadIdx.x;
-        bool ok = e < me;
-        bool keep = false;
-        int32_t a = 0, b = 0;
-        int64_t x = 0;
-        if (ok) {
-            a = eu[e]; b = ev[e];
-            x = ew ? ew[e] : 1;
-            bool ra = rr[a] == r, rb = rr[b] == r;
-            if (ra || rb) {
-                acc += (unsigned long long)x;
-                if (!ra) atomicAdd(&deg[a], (unsigned long long)(-x));
-                if (!rb) atomicAdd(&deg[b], (unsigned long long)(-x));
+    for (int64_t tb = (int64_t)blockIdx.x * kPruneTile; tb < me; tb += (int64_t)gridDim.x * kPruneTile) {
+        int32_t a[kPruneItems], b[kPruneItems];
+        int64_t x[kPruneItems];
+        unsigned keepm = 0;
+#pragma unroll
+        for (int i = 0; i < kPruneItems; ++i) {
+            const int64_t e = tb + (int64_t)i * kT + threadIdx.x;
+            const bool ok = e < me;
+            a[i] = ok ? eu[e] : -1;
+            b[i] = ok ? ev[e] : -1;
+            x[i] = ok ? (ew ? ew[e] : 1) : 0;
+            const bool ra = ok && rr[a[i]] == r, rb = ok && rr[b[i]] == r;
+            if (ra || rb) acc += (unsigned long long)x[i];
+            const int32_t da = (ok && rb && !ra) ? a[i] : -1;   // surviving end of a removed edge
+            const int32_t db = (ok && ra && !rb) ? b[i] : -1;
+            if (ew) {
+                if (da >= 0) atomicAdd(&deg[da], (unsigned long long)(-x[i]));
+                if (db >= 0) atomicAdd(&deg[db], (unsigned long long)(-x[i]));
             } else {
-                keep = true;
+                warp_add<unsigned long long>(deg, da, ~0ull);   // -1 per edge, modulo 2^64
+                warp_add<unsigned long long>(deg, db, ~0ull);
             }
+            if (ok && !ra && !rb) keepm |= 1u << i;
         }
-        unsigned bal = __ballot_sync(0xffffffffu, keep);
-        unsigned long long slot = 0;
-        if (lane_id() == 0 && bal) slot = atomicAdd(ncount, (unsigned long long)__popc(bal));
-        slot = __shfl_sync(0xffffffffu, slot, 0);
-        if (keep) {
-            unsigned long long p = slot + __popc(bal & ((1u << lane_id()) - 1u));
-            nu[p] = a; nv[p] = b;
-            if (nw) nw[p] = x;
+        int32_t total = 0;
+        const int32_t off = block_excl_scan<int32_t>(__popc(keepm), sh_scan, &total);
+        if (threadIdx.x == 0) sh_base = total ? atomicAdd(ncount, (unsigned long long)total) : 0ull;
+        __syncthreads();
+        unsigned long long p = sh_base + (unsigned long long)off;
+        __syncthreads();   // sh_base is rewritten by the next tile
+#pragma unroll
+        for (int i = 0; i < kPruneItems; ++i) {
+            if (keepm & (1u << i)) {
+                nu[p] = a[i]; nv[p] = b[i];
+                if (nw) nw[p] = x[i];
+                ++p;
+            }
         }
     }
     acc = warp_sum(acc);
@@ -263,15 +325,14 @@ lowd_status lowd_graph_load(lowd_ctx* h, const int32_t* du, const int32_t* dv, c
         dfree(&first); dfree(&pos);
     };
     do {
-        if ((s = dalloc(h, &keys[0], m_in))) break;
-        if ((s = dalloc(h, &idx[0], m_in))) break;
         if ((s = dalloc(h, &h->d_i32, 16))) break;
         if ((s = dalloc(h, &h->d_i64, 16))) break;
         if ((s = dalloc(h, &h->d_stats, 16))) break;
         if (cudaMallocHost(&h->h_pin, 16 * sizeof(int64_t)) != cudaSuccess) { s = h->fail(cudaErrorMemoryAllocation); break; }
         cudaMemsetAsync(h->d_i32, 0, 16 * sizeof(int32_t), st);
-        if (m_in > 0) {
-            LOWD_LAUNCH(k_check_keys, grid_for(m_in), kT, 0, st, du, dv, dw, m_in, n, keys[0], idx[0], h->d_i32);
+        if (m_in > 0) {   // checks only: keys are written only if the input needs sorting
+            LOWD_LAUNCH(k_check_keys, grid_for(m_in), kT, 0, st, du, dv, dw, m_in, n, (uint64_t*)nullptr,
+                        (uint32_t*)nullptr, h->d_i32);
         }
         if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
         int32_t err = 0;
@@ -293,6 +354,9 @@ lowd_status lowd_graph_load(lowd_ctx* h, const int32_t* du, const int32_t* dv, c
         int64_t m = m_in;
         const bool sorted = !(err & UNSORTED);
         if (!sorted && m_in > 1) {
+            if ((s = dalloc(h, &keys[0], m_in))) break;
+            if ((s = dalloc(h, &idx[0], m_in))) break;
+            LOWD_LAUNCH(k_check_keys, grid_for(m_in), kT, 0, st, du, dv, dw, m_in, n, keys[0], idx[0], h->d_i32 + 6);
             if ((s = dalloc(h, &keys[1], m_in))) break;
             if ((s = dalloc(h, &idx[1], m_in))) break;
             if ((s = h->need_tmp(lowd_sort_tmp_bytes(m_in)))) break;
@@ -316,9 +380,11 @@ lowd_status lowd_graph_load(lowd_ctx* h, const int32_t* du, const int32_t* dv, c
             if ((s = dalloc(h, &h->w, m))) break;
             if ((s = dalloc(h, &h->wu, m))) break;
         }
-        if (m_in > 0)
+        if (m_in > 0 && keys[0] == nullptr)   // already canonical order: a direct copy
+            LOWD_LAUNCH(k_emit_sorted, grid_for(m_in), kT, 0, st, du, dv, dw, m_in, h->u, h->v, h->w, h->wu);
+        else if (m_in > 0)
             LOWD_LAUNCH(k_emit_unique, grid_for(m_in), kT, 0, st, keys[cur], idx[cur], first, pos, m_in, n, dw,
-                                                         h->u, h->v, h->w, h->wu);
+                        h->u, h->v, h->w, h->wu);
         if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
         s = lowd_graph_max_degree(h);
     } while (0);
@@ -430,7 +496,8 @@ lowd_status lowd_graph_prune(lowd_ctx* h, int32_t* rounds_out) {
             cudaMemsetAsync(h->d_i64 + 4, 0, 3 * sizeof(int64_t), st);
             LOWD_LAUNCH(k_prune_mark, grid_for(nact), kT, 0, st, act, nact, deg, N, W, rnext, h->removal_round, keep, removed);
             if (me > 0)
-                LOWD_LAUNCH(k_prune_edges, grid_for(me), kT, 0, st, cu_, cv_, cw_, me, rnext, h->removal_round, deg,
+                LOWD_LAUNCH(k_prune_edges, lowd_grid_for(me, kPruneTile, 4), kT, 0, st, cu_, cv_, cw_, me, rnext,
+                            h->removal_round, deg,
                                                            removedW, eu[nxt], ev[nxt], ew[nxt], ncount);
             if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
             if (cudaMemcpyAsync(h->h_pin, h->d_i64 + 4, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
