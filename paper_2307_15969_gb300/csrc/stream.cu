@@ -147,7 +147,7 @@ __device__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned n
             uint32_t spins = 0;
             while (*gen == g) {
                 if (++spins > kGridSpins) { ok = false; atomicOr(err, 2); break; }
-                __nanosleep(64);
+                if (spins > 4096) __nanosleep(64);   // poll fast at first, then back off
             }
         }
         __threadfence();
@@ -229,8 +229,9 @@ enum { WB_ALWAYS = 0, WB_NEVER = 1, WB_LAST_PASS = 2 };
 constexpr uint32_t kZeroSlot = 0;   // ring offset of an always-zero load (padding ends)
 constexpr uint32_t kRingHead = 128; // stages start here
 
-constexpr int kSegs = 16;           // classes (or class pieces) per chunk
-constexpr int kHdrInts = 20;        // chunk header: begin, padded size, segment count, 16 ends
+constexpr int kSegs = 64;           // classes (or class pieces) per chunk
+constexpr int kHdrInts = 68;        // chunk header: begin, padded size, segment count, 64 ends, pad
+constexpr int kSmallSeg = 32;       // segments this small are updated by one warp
 constexpr int kConsumers = 512;
 constexpr int kProducerWarps = 2;
 constexpr int kStoreGroups = 8;
@@ -245,7 +246,7 @@ __host__ __device__ inline StreamLayout stream_layout(uint32_t E, bool weighted)
     StreamLayout L;
     L.E = E;
     L.hdr = 0;
-    L.ea = 128;
+    L.ea = 4 * kHdrInts <= 128 ? 128 : ((4 * kHdrInts + 127) & ~127);
     L.eb = L.ea + 4 * E;
     L.s = L.eb + 4 * E;
     L.sa = L.s + 4 * E;
@@ -659,9 +660,14 @@ k_sweep_stream(int32_t n, int32_t NC, const int32_t* __restrict__ ctab, const in
         float2* lb = reinterpret_cast<float2*>(st + L.lb);
         const int32_t nseg = min(hdr[2], kSegs);
         int32_t cb = 0;
+        int32_t ce = nseg > 0 ? min(hdr[3], (int32_t)E) : 0;
         for (int32_t g = 0; g < nseg; ++g) {
-            const int32_t ce = min(hdr[3 + g], (int32_t)E);
-            for (int32_t r = cb + tid; r < ce; r += nc) {
+            // a small segment is updated by warp 0 alone; consecutive small segments are
+            // separated by a warp barrier, any other pair by the consumer barrier
+            const bool small = ce - cb <= kSmallSeg;
+            const int32_t cn = g + 1 < nseg ? min(hdr[4 + g], (int32_t)E) : ce;
+            const bool next_small = cn - ce <= kSmallSeg;
+            for (int32_t r = cb + tid; r < ce && (!small || tid < 32); r += nc) {
                 const uint32_t wa = ssa[r], wb = ssb[r];
                 uint32_t oa = (first && (wa & kWrap)) ? own0 + L.la + 8u * r : (wa & kOffMask);
                 uint32_t ob = (first && (wb & kWrap)) ? own0 + L.lb + 8u * r : (wb & kOffMask);
@@ -676,7 +682,14 @@ k_sweep_stream(int32_t n, int32_t NC, const int32_t* __restrict__ ctab, const in
                 ss[r] = ns;
             }
             cb = ce;
-            if (g + 1 < nseg) consumer_sync(nc);
+            ce = cn;
+            if (g + 1 < nseg) {
+                if (small && next_small) {
+                    if (tid < 32) __syncwarp();
+                } else {
+                    consumer_sync(nc);
+                }
+            }
         }
         fence_proxy_async_smem();   // the splits leave by a bulk store (async proxy)
         bool fail = false;
@@ -696,7 +709,7 @@ k_sweep_stream(int32_t n, int32_t NC, const int32_t* __restrict__ ctab, const in
 // thread takes edges of the class, reads both loads from global memory (L2, bypassing L1),
 // updates and writes them back; a grid barrier separates the classes.  The remaining classes
 // (the long tail of small classes around the hubs) go through k_sweep_stream.
-constexpr int kGridThreads = 512;
+constexpr int kGridThreads = 1024;
 constexpr int32_t kGridMinClass = 1024;   // classes at least this large take a grid-wide step
 
 template <bool WEIGHTED>
@@ -706,18 +719,39 @@ k_sweep_grid(int32_t K, const int32_t* __restrict__ coff, const int32_t* __restr
              float2* __restrict__ lp, unsigned* __restrict__ bar, int32_t* __restrict__ err) {
     const int64_t T = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // the ends, split and weight of this thread's first edge of the next class are read before
+    // the grid barrier (they do not depend on the loads), so a class costs one round trip
+    int32_t b0 = K > 0 ? __ldg(coff) : 0;
+    int32_t na = 0, nb = 0;
+    float nsplit = 0.0f, nw = 1.0f;
+    auto fetch = [&](int64_t i, int32_t end) {
+        if (i < end) {
+            na = __ldg(ea + i);
+            nb = __ldg(eb + i);
+            nsplit = __ldcg(cs + i);
+            nw = WEIGHTED ? __ldg(cw + i) : 1.0f;
+        }
+    };
+    if (K > 0) fetch(b0 + t0, __ldg(coff + 1));
     for (int32_t c = 0; c < K; ++c) {
-        const int32_t b0 = __ldg(coff + c), b1 = __ldg(coff + c + 1);
+        const int32_t b1 = __ldg(coff + c + 1);
         for (int64_t i = b0 + t0; i < b1; i += T) {
-            const int32_t a = __ldg(ea + i), b = __ldg(eb + i);
+            int32_t a, b;
+            float s, w;
+            if (i == b0 + t0) {
+                a = na; b = nb; s = nsplit; w = nw;
+            } else {
+                a = __ldg(ea + i); b = __ldg(eb + i); s = __ldcg(cs + i);
+                w = WEIGHTED ? __ldg(cw + i) : 1.0f;
+            }
             float2 A = __ldcg(lp + a), B = __ldcg(lp + b);
-            const float s = __ldcg(cs + i);
-            const float w = WEIGHTED ? __ldg(cw + i) : 1.0f;
             const float ns = comp_transfer(A, B, s, w);
             __stcg(lp + a, A);
             __stcg(lp + b, B);
             __stcg(cs + i, ns);
         }
+        b0 = b1;
+        if (c + 1 < K) fetch(b0 + t0, __ldg(coff + c + 2));
         if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
     }
 }
@@ -993,7 +1027,7 @@ cudaError_t lowd_stream_passes(lowd_ctx* h, int32_t passes) {
         auto gk = weighted ? k_sweep_grid<true> : k_sweep_grid<false>;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gk, kGridThreads, 0);
-        const int blocks = lowd_device_sms() * (per_sm > 2 ? 2 : (per_sm > 0 ? per_sm : 1));
+        const int blocks = lowd_device_sms() * (per_sm > 0 ? 1 : 1);   // one block per SM
         int32_t K = h->s2_K;
         const int32_t* coff = h->coff_real;
         const int32_t* pea = h->s2_ea;
