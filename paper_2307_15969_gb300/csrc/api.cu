@@ -47,7 +47,7 @@ void free_all(lowd_ctx* h) {
     dfree(&h->perm); dfree(&h->coff); dfree(&h->coff_real); dfree(&h->cuv); dfree(&h->crk);
     dfree(&h->cw); dfree(&h->cs); dfree(&h->l); dfree(&h->l_lo);
     dfree(&h->s2_ctab); dfree(&h->s2_beg); dfree(&h->s2_ea); dfree(&h->s2_eb);
-    dfree(&h->s2_srcA); dfree(&h->s2_srcB); dfree(&h->s2_lp);
+    dfree(&h->s2_srcA); dfree(&h->s2_srcB); dfree(&h->s2_lp); dfree(&h->s2_blob); dfree(&h->s2_blobo);
     dfree(&h->tmp); h->tmp_cap = 0;
     dfree(&h->d_stats); dfree(&h->d_i64); dfree(&h->d_i32);
     if (h->h_pin) cudaFreeHost(h->h_pin);

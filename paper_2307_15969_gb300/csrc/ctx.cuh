@@ -77,6 +77,8 @@ struct lowd_ctx {
     uint32_t* s2_srcA = nullptr;  // [m_pad] read descriptors of the two ends
     uint32_t* s2_srcB = nullptr;
     float2* s2_lp = nullptr;      // [n + 1] loads as (hi, lo) pairs during the passes
+    uint32_t* s2_blob = nullptr;  // per chunk: header, ends, read descriptors (, weights)
+    int64_t* s2_blobo = nullptr;  // [NC + 1] word offsets of the chunk blobs
 
     // scratch
     void* tmp = nullptr;

@@ -237,31 +237,55 @@ constexpr int kProducerWarps = 2;
 constexpr int kStoreGroups = 8;
 constexpr int kLead = 3;            // D: chunks gathered ahead of the consumers; S = 2D stages
 
+// A stage: the chunk's blob (header, then ends a and b, read descriptors a and b and, if
+// weighted, weights, each an array of the chunk's padded size), then the splits and the two
+// gathered-or-updated load slots per edge at fixed offsets (read descriptors point there).
 struct StreamLayout {
     uint32_t E;          // edges per stage (multiple of 4)
-    uint32_t hdr, ea, eb, s, sa, sb, w, la, lb, bytes;   // offsets inside a stage
+    uint32_t blob, s, la, lb, bytes;   // offsets inside a stage
 };
+
+__host__ __device__ inline uint32_t blob_words(uint32_t Ej, bool weighted) {
+    return (uint32_t)kHdrInts + (weighted ? 5u : 4u) * Ej;
+}
 
 __host__ __device__ inline StreamLayout stream_layout(uint32_t E, bool weighted) {
     StreamLayout L;
     L.E = E;
-    L.hdr = 0;
-    L.ea = 4 * kHdrInts <= 128 ? 128 : ((4 * kHdrInts + 127) & ~127);
-    L.eb = L.ea + 4 * E;
-    L.s = L.eb + 4 * E;
-    L.sa = L.s + 4 * E;
-    L.sb = L.sa + 4 * E;
-    L.w = L.sb + 4 * E;
-    L.la = weighted ? L.w + 4 * E : L.w;
-    L.la = (L.la + 15u) & ~15u;
-    L.lb = L.la + 8 * E;
-    L.bytes = ((L.lb + 8 * E) + 127u) & ~127u;
+    L.blob = 0;
+    L.s = (4u * blob_words(E, weighted) + 127u) & ~127u;
+    L.la = (L.s + 4u * E + 15u) & ~15u;
+    L.lb = L.la + 8u * E;
+    L.bytes = ((L.lb + 8u * E) + 127u) & ~127u;
     return L;
+}
+
+// views into a stage whose blob has landed (Ej = the chunk's padded size)
+struct StageView {
+    const int32_t* hdr;
+    const int32_t* ea;
+    const int32_t* eb;
+    const uint32_t* sa;
+    const uint32_t* sb;
+    const float* w;
+    uint32_t cnt;
+};
+
+__device__ __forceinline__ StageView stage_view(const unsigned char* st, uint32_t E) {
+    StageView v;
+    v.hdr = reinterpret_cast<const int32_t*>(st);
+    v.cnt = min((uint32_t)v.hdr[1], E);
+    v.ea = v.hdr + kHdrInts;
+    v.eb = v.ea + v.cnt;
+    v.sa = reinterpret_cast<const uint32_t*>(v.eb + v.cnt);
+    v.sb = v.sa + v.cnt;
+    v.w = reinterpret_cast<const float*>(v.sb + v.cnt);
+    return v;
 }
 
 // largest E (multiple of 4) whose S stages fit the shared-memory budget
 inline uint32_t stream_edges_per_stage(int S, bool weighted, size_t budget) {
-    uint32_t E = (uint32_t)(budget / (size_t)S / (weighted ? 40u : 36u)) & ~3u;
+    uint32_t E = (uint32_t)(budget / (size_t)S / (weighted ? 40u : 36u)) & ~3u;   // 16 B loads + 20/24 B
     while (E > 4 && (size_t)stream_layout(E, weighted).bytes * (size_t)S > budget) E -= 4;
     return E;
 }
@@ -386,6 +410,35 @@ __global__ void k_descriptors(const uint32_t* __restrict__ key, const int64_t* _
     }
 }
 
+// chunk blobs: header row, then ends a, ends b, read descriptors a, b (and weights) of the
+// chunk's padded positions
+__global__ void k_blob_headers(const int32_t* __restrict__ ctab, const int64_t* __restrict__ blob_off, int32_t NC,
+                               uint32_t* __restrict__ blob) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)NC * kHdrInts;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t J = i / kHdrInts, k = i % kHdrInts;
+        blob[blob_off[J] + k] = (uint32_t)ctab[i];
+    }
+}
+
+__global__ void k_blob_data(const int32_t* __restrict__ beg, const int64_t* __restrict__ blob_off, int32_t NC,
+                            int64_t p0, int64_t m_pad, const int32_t* __restrict__ ea, const int32_t* __restrict__ eb,
+                            const uint32_t* __restrict__ srcA, const uint32_t* __restrict__ srcB,
+                            const float* __restrict__ cw, uint32_t* __restrict__ blob) {
+    for (int64_t p = p0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m_pad;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t J = chunk_of(beg, NC, p);
+        const int64_t Ej = beg[J + 1] - beg[J];
+        const int64_t i = p - beg[J];
+        uint32_t* d = blob + blob_off[J] + kHdrInts;
+        d[i] = (uint32_t)ea[p];
+        d[Ej + i] = (uint32_t)eb[p];
+        d[2 * Ej + i] = srcA[p];
+        d[3 * Ej + i] = srcB[p];
+        if (cw) d[4 * Ej + i] = __float_as_uint(cw[p]);
+    }
+}
+
 __global__ void k_pack_loads(const float* __restrict__ l, const float* __restrict__ l_lo, int32_t n,
                              float2* __restrict__ lp) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n;
@@ -464,12 +517,11 @@ __device__ __forceinline__ void producer_sync() {
 
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(kConsumers + kProducerWarps * 32, 1)
-k_sweep_stream(int32_t n, int32_t NC, const int32_t* __restrict__ ctab, const int32_t* __restrict__ ea,
-               const int32_t* __restrict__ eb, const uint32_t* __restrict__ srcA, const uint32_t* __restrict__ srcB,
-               const float* __restrict__ cw, float* __restrict__ cs, float2* __restrict__ lp, int32_t passes,
-               int32_t S, int32_t D, uint32_t E, uint32_t smem_bytes, int32_t* __restrict__ err) {
+k_sweep_stream(int32_t n, int32_t NC, const int64_t* __restrict__ blob_off, const int32_t* __restrict__ beg,
+               const uint32_t* __restrict__ blob, float* __restrict__ cs, float2* __restrict__ lp,
+               int32_t passes, int32_t S, int32_t D, uint32_t E, uint32_t smem_bytes, int32_t* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char ring[];
-    __shared__ __align__(8) uint64_t mfull[16];   // stage's streams and header landed (bulk copies)
+    __shared__ __align__(8) uint64_t mfull[16];   // stage's blob and splits landed (bulk copies)
     __shared__ __align__(8) uint64_t gfull[16];   // stage's gathered loads landed (cp.async)
     __shared__ __align__(8) uint64_t empty[16];   // stage released by the consumers
     __shared__ volatile int32_t abort_flag;
@@ -494,39 +546,28 @@ k_sweep_stream(int32_t n, int32_t NC, const int32_t* __restrict__ ctab, const in
     if (tid >= nc) {
         // ---------------- producers
         const int pt = tid - nc;
-        // chunk q's header and streams, by bulk copies (one thread); b0, b1 = its padded range
-        auto meta = [&](int32_t q, int32_t b0, int32_t b1) {
+        struct Range { int64_t o0, o1; int32_t b0, b1; };
+        // chunk q's blob and splits, by two bulk copies (one thread)
+        auto meta = [&](int32_t q, const Range& r) {
             if (pt != 0) return;
-            const int32_t J = q % NC;
             unsigned char* st = stage(q);
             uint64_t* bar = &mfull[q % S];
-            const uint32_t bytes = 4u * (uint32_t)(b1 - b0);
-            mbar_expect_tx(bar, 4u * kHdrInts + bytes * (WEIGHTED ? 6u : 5u));
-            bulk_g2s(st + L.hdr, ctab + (int64_t)J * kHdrInts, 4u * kHdrInts, bar);
-            if (bytes) {
-                bulk_g2s(st + L.ea, ea + b0, bytes, bar);
-                bulk_g2s(st + L.eb, eb + b0, bytes, bar);
-                bulk_g2s(st + L.s, cs + b0, bytes, bar);
-                bulk_g2s(st + L.sa, srcA + b0, bytes, bar);
-                bulk_g2s(st + L.sb, srcB + b0, bytes, bar);
-                if (WEIGHTED) bulk_g2s(st + L.w, cw + b0, bytes, bar);
-            }
+            const uint32_t bb = 4u * (uint32_t)(r.o1 - r.o0);
+            const uint32_t sb = 4u * (uint32_t)(r.b1 - r.b0);
+            mbar_expect_tx(bar, bb + sb);
+            bulk_g2s(st + L.blob, blob + r.o0, bb, bar);
+            if (sb) bulk_g2s(st + L.s, cs + r.b0, sb, bar);
         };
-        // gathers of the loads chunk q's descriptors ask for (its streams already landed)
+        // gathers of the loads chunk q's descriptors ask for (its blob already landed)
         auto gather = [&](int32_t q) {
             unsigned char* st = stage(q);
             const bool first = q < NC;
-            const int32_t* hdr = reinterpret_cast<const int32_t*>(st + L.hdr);
-            const uint32_t cnt = min((uint32_t)hdr[1], E);
-            const int32_t* sea = reinterpret_cast<const int32_t*>(st + L.ea);
-            const int32_t* seb = reinterpret_cast<const int32_t*>(st + L.eb);
-            const uint32_t* ssa = reinterpret_cast<const uint32_t*>(st + L.sa);
-            const uint32_t* ssb = reinterpret_cast<const uint32_t*>(st + L.sb);
+            const StageView v = stage_view(st, E);
             const uint32_t own0 = (uint32_t)(st - ring);
-            for (uint32_t i = pt; i < cnt; i += NP) {
-                const uint32_t wa = ssa[i], wb = ssb[i];
+            for (uint32_t i = pt; i < v.cnt; i += NP) {
+                const uint32_t wa = v.sa[i], wb = v.sb[i];
                 const uint32_t oa = own0 + L.la + 8u * i, ob = own0 + L.lb + 8u * i;
-                const int32_t a = sea[i], b = seb[i];
+                const int32_t a = v.ea[i], b = v.eb[i];
                 if (((wa & kOffMask) == oa || (first && (wa & kWrap))) && (uint32_t)a < (uint32_t)n)
                     cp_async8(ring + oa, lp + a);
                 if (((wb & kOffMask) == ob || (first && (wb & kWrap))) && (uint32_t)b < (uint32_t)n)
@@ -537,24 +578,19 @@ k_sweep_stream(int32_t n, int32_t NC, const int32_t* __restrict__ ctab, const in
         // released chunk q: loads back to global memory, splits by a bulk store
         auto writeback = [&](int32_t q) {
             unsigned char* st = stage(q);
-            const int32_t* hdr = reinterpret_cast<const int32_t*>(st + L.hdr);
-            const int32_t b0 = hdr[0];
-            const uint32_t cnt = min((uint32_t)hdr[1], E);
+            const StageView v = stage_view(st, E);
+            const int32_t b0 = v.hdr[0];
             const bool lastp = q >= P - NC;
-            const int32_t* sea = reinterpret_cast<const int32_t*>(st + L.ea);
-            const int32_t* seb = reinterpret_cast<const int32_t*>(st + L.eb);
-            const uint32_t* ssa = reinterpret_cast<const uint32_t*>(st + L.sa);
-            const uint32_t* ssb = reinterpret_cast<const uint32_t*>(st + L.sb);
             const float2* la = reinterpret_cast<const float2*>(st + L.la);
             const float2* lb = reinterpret_cast<const float2*>(st + L.lb);
-            for (uint32_t i = pt; i < cnt; i += NP) {
-                const uint32_t ca = ssa[i] >> kWbShift, cb = ssb[i] >> kWbShift;
-                const int32_t a = sea[i], b = seb[i];
+            for (uint32_t i = pt; i < v.cnt; i += NP) {
+                const uint32_t ca = v.sa[i] >> kWbShift, cb = v.sb[i] >> kWbShift;
+                const int32_t a = v.ea[i], b = v.eb[i];
                 if ((ca == WB_ALWAYS || (ca == WB_LAST_PASS && lastp)) && (uint32_t)a < (uint32_t)n) lp[a] = la[i];
                 if ((cb == WB_ALWAYS || (cb == WB_LAST_PASS && lastp)) && (uint32_t)b < (uint32_t)n) lp[b] = lb[i];
             }
-            if (pt == 0 && cnt) {
-                bulk_s2g(cs + b0, st + L.s, 4u * cnt);
+            if (pt == 0 && v.cnt) {
+                bulk_s2g(cs + b0, st + L.s, 4u * v.cnt);
                 bulk_commit();
             }
         };
@@ -564,23 +600,27 @@ k_sweep_stream(int32_t n, int32_t NC, const int32_t* __restrict__ ctab, const in
             while (!ok && !abort_flag && ++spins < kSpinLimit) ok = mbar_try_wait(bar, par);
             return ok;
         };
-        // chunk ranges, fetched one step ahead of their meta copy
-        auto range = [&](int32_t q, int32_t& b0, int32_t& b1) {
+        // chunk ranges, read one step ahead of their copy
+        auto range = [&](int32_t q) -> Range {
             const int32_t J = q % NC;
-            b0 = __ldg(ctab + (int64_t)J * kHdrInts);
-            b1 = b0 + __ldg(ctab + (int64_t)J * kHdrInts + 1);
+            Range r;
+            r.o0 = __ldg(blob_off + J);
+            r.o1 = __ldg(blob_off + J + 1);
+            r.b0 = __ldg(beg + J);
+            r.b1 = __ldg(beg + J + 1);
+            return r;
         };
-        int32_t mf = 0, gf = 0;   // next chunk to copy, next chunk to gather
-        int32_t nb0 = 0, nb1 = 0;
-        bool ok = true;
-        if (P > 0) range(0, nb0, nb1);
-        while (mf <= D && mf < P) {
-            meta(mf, nb0, nb1);
-            if (++mf < P) range(mf, nb0, nb1);
+        // copies run D + 2 chunks ahead of the consumers, gathers D chunks ahead
+        int32_t mf = 0, gf = 0;
+        Range nr{};
+        if (P > 0) nr = range(0);
+        while (mf < D + 2 && mf < P) {
+            meta(mf, nr);
+            if (++mf < P) nr = range(mf);
         }
+        bool ok = true;
         while (gf < D && gf < P && ok) {
             if (pt == 0) ok = wait_bar(&mfull[gf % S], (uint32_t)((gf / S) & 1));
-            producer_sync();
             if (pt == 0 && !ok) abort_flag = 1;
             producer_sync();
             if (abort_flag) break;
@@ -594,18 +634,18 @@ k_sweep_stream(int32_t n, int32_t NC, const int32_t* __restrict__ ctab, const in
             if (abort_flag) break;
             writeback(q);
             if (mf < P) {
-                // the stage of chunk mf held chunk mf - S (released, written back): its split
-                // store must have finished reading it, and every store older than the last
-                // kStoreGroups must be complete (a chunk's splits are read again a pass later)
+                // the stage of chunk mf held chunk mf - S = q - 1 (released, written back):
+                // its split store (committed one iteration ago) must have finished reading it,
+                // and every store older than the last kStoreGroups must be complete (a
+                // chunk's splits are read again a pass later)
                 if (pt == 0) {
-                    // the stage's last split store was committed D - 1 iterations ago
                     bulk_wait<kStoreGroups>();
-                    bulk_wait_read<kLead - 1>();
+                    bulk_wait_read<1>();
                 }
                 fence_proxy_async_smem();   // generic reads of the stage before async writes
                 producer_sync();
-                meta(mf, nb0, nb1);
-                if (++mf < P) range(mf, nb0, nb1);
+                meta(mf, nr);
+                if (++mf < P) nr = range(mf);
             }
             if (gf < P) {
                 bool okg = true;
@@ -651,32 +691,30 @@ k_sweep_stream(int32_t n, int32_t NC, const int32_t* __restrict__ ctab, const in
         const bool first = q < NC;
         unsigned char* st = stage(q);
         const uint32_t own0 = (uint32_t)(st - ring);
-        const int32_t* hdr = reinterpret_cast<const int32_t*>(st + L.hdr);
-        const uint32_t* ssa = reinterpret_cast<const uint32_t*>(st + L.sa);
-        const uint32_t* ssb = reinterpret_cast<const uint32_t*>(st + L.sb);
+        const StageView v = stage_view(st, E);
         float* ss = reinterpret_cast<float*>(st + L.s);
-        const float* sw = reinterpret_cast<const float*>(st + L.w);
         float2* la = reinterpret_cast<float2*>(st + L.la);
         float2* lb = reinterpret_cast<float2*>(st + L.lb);
-        const int32_t nseg = min(hdr[2], kSegs);
+        const int32_t nseg = min(v.hdr[2], kSegs);
+        const int32_t cmax = (int32_t)v.cnt;
         int32_t cb = 0;
-        int32_t ce = nseg > 0 ? min(hdr[3], (int32_t)E) : 0;
+        int32_t ce = nseg > 0 ? min(v.hdr[3], cmax) : 0;
         for (int32_t g = 0; g < nseg; ++g) {
             // a small segment is updated by warp 0 alone; consecutive small segments are
             // separated by a warp barrier, any other pair by the consumer barrier
             const bool small = ce - cb <= kSmallSeg;
-            const int32_t cn = g + 1 < nseg ? min(hdr[4 + g], (int32_t)E) : ce;
+            const int32_t cn = g + 1 < nseg ? min(v.hdr[4 + g], cmax) : ce;
             const bool next_small = cn - ce <= kSmallSeg;
             for (int32_t r = cb + tid; r < ce && (!small || tid < 32); r += nc) {
-                const uint32_t wa = ssa[r], wb = ssb[r];
+                const uint32_t wa = v.sa[r], wb = v.sb[r];
                 uint32_t oa = (first && (wa & kWrap)) ? own0 + L.la + 8u * r : (wa & kOffMask);
                 uint32_t ob = (first && (wb & kWrap)) ? own0 + L.lb + 8u * r : (wb & kOffMask);
                 if (oa > lim || ob > lim) { oob = true; oa = kZeroSlot; ob = kZeroSlot; }
                 float2 A = *reinterpret_cast<const float2*>(ring + oa);
                 float2 B = *reinterpret_cast<const float2*>(ring + ob);
-                const float s = ss[r];
-                const float w = WEIGHTED ? sw[r] : 1.0f;
-                const float ns = comp_transfer(A, B, s, w);
+                const float sv = ss[r];
+                const float wv = WEIGHTED ? v.w[r] : 1.0f;
+                const float ns = comp_transfer(A, B, sv, wv);
                 la[r] = A;
                 lb[r] = B;
                 ss[r] = ns;
@@ -921,7 +959,7 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
         // pad the chunk count: a multiple of S (a chunk keeps its stage across passes), and
         // enough chunks that a chunk's split store completes before the chunk is read again
         int32_t NC = (int32_t)real_beg.size();
-        int32_t NCp = NC < D + kStoreGroups + 2 ? D + kStoreGroups + 2 : NC;
+        int32_t NCp = NC < D + kStoreGroups + 3 ? D + kStoreGroups + 3 : NC;
         NCp = (NCp + S - 1) / S * S;
         while ((int32_t)real_beg.size() < NCp) { open(); close(); }
         std::vector<int32_t> pad_beg;
@@ -977,6 +1015,20 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
             LOWD_LAUNCH(k_descriptors, grid_for(2 * m_pad), kT, 0, st, sk, sv, 2 * m_pad, (uint32_t)n, gfirst, glast,
                         h->s2_beg, NCp, S, D, L, h->s2_srcA, h->s2_srcB);
         }
+        // ---- 8. chunk blobs (what the pass kernel copies per chunk)
+        {
+            std::vector<int64_t> bo((size_t)NCp + 1, 0);
+            for (int32_t J = 0; J < NCp; ++J)
+                bo[(size_t)J + 1] = bo[(size_t)J] + blob_words((uint32_t)(pad_beg[(size_t)J + 1] - pad_beg[(size_t)J]), weighted);
+            if ((s = dalloc(h, &h->s2_blobo, (size_t)NCp + 1))) break;
+            if ((s = dalloc(h, &h->s2_blob, (size_t)bo[(size_t)NCp]))) break;
+            cudaMemcpyAsync(h->s2_blobo, bo.data(), sizeof(int64_t) * bo.size(), cudaMemcpyHostToDevice, st);
+            LOWD_LAUNCH(k_blob_headers, grid_for((int64_t)NCp * kHdrInts), kT, 0, st, h->s2_ctab, h->s2_blobo, NCp,
+                        h->s2_blob);
+            if (m_pad > grid_pad)
+                LOWD_LAUNCH(k_blob_data, grid_for(m_pad - grid_pad), kT, 0, st, h->s2_beg, h->s2_blobo, NCp, grid_pad,
+                            m_pad, h->s2_ea, h->s2_eb, h->s2_srcA, h->s2_srcB, h->cw, h->s2_blob);
+        }
         if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { s = h->fail(e); break; }
@@ -1009,9 +1061,9 @@ cudaError_t lowd_stream_passes(lowd_ctx* h, int32_t passes) {
     h->sweep_E = 0;
     LOWD_LAUNCH(k_pack_loads, grid_for((int64_t)h->n + 1), kT, 0, h->st, h->l, h->l_lo, h->n, h->s2_lp);
     auto stream_launch = [&](int32_t k) {
-        LOWD_LAUNCH(kern, 1, kConsumers + kProducerWarps * 32, smem, h->st, h->n, h->s2_NC, h->s2_ctab, h->s2_ea,
-                    h->s2_eb, h->s2_srcA, h->s2_srcB, h->cw, h->cs, h->s2_lp, k, h->s2_S, h->s2_D,
-                    (uint32_t)h->s2_E, (uint32_t)smem, h->d_i32 + 8);
+        LOWD_LAUNCH(kern, 1, kConsumers + kProducerWarps * 32, smem, h->st, h->n, h->s2_NC, h->s2_blobo, h->s2_beg,
+                    h->s2_blob, h->cs, h->s2_lp, k, h->s2_S, h->s2_D, (uint32_t)h->s2_E, (uint32_t)smem,
+                    h->d_i32 + 8);
         return cudaGetLastError();
     };
     cudaMemsetAsync(h->d_i32 + 12, 0, 2 * sizeof(int32_t), h->st);   // grid barrier words
