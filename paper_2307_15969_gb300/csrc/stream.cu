@@ -748,7 +748,11 @@ k_sweep_stream(int32_t n, int32_t NC, const int64_t* __restrict__ blob_off, cons
 // updates and writes them back; a grid barrier separates the classes.  The remaining classes
 // (the long tail of small classes around the hubs) go through k_sweep_stream.
 constexpr int kGridThreads = 1024;
-constexpr int32_t kGridMinClass = 1024;   // classes at least this large take a grid-wide step
+// A grid-wide step costs about one grid barrier plus one memory round trip (~3 us) whatever
+// the class size; the one-CTA stream moves about one tail edge per 17 ns (it is bound by the
+// scattered 8-byte gathers and write-backs of a single SM).  Classes above ~3 us / 17 ns
+// edges are cheaper as grid steps.
+constexpr int32_t kGridMinClass = 192;    // classes at least this large take a grid-wide step
 
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(kGridThreads)

@@ -541,6 +541,23 @@ k_sweep_tma(int32_t n, int32_t C, const int32_t* __restrict__ coff, const uint32
         int32_t cb = 0;
         for (int32_t c = c0; c < c1; ++c) {
             const int32_t ce = __shfl_sync(0xffffffffu, off_cur, c - c0 + 1) - base;
+            if (E == 1) {
+                // one edge per thread: the class fits the consumer threads
+                const int32_t r = cb + tid;
+                if (r < ce) {
+                    const uint32_t uv = suv[r];
+                    float2* pa = L + end_a(uv);
+                    float2* pb = L + end_b(uv);
+                    float2 A = *pa, Bv = *pb;
+                    const float ns = comp_transfer(A, Bv, ss[r], WEIGHTED ? sw[r] : 1.0f);
+                    *pa = A;
+                    *pb = Bv;
+                    ss[r] = ns;
+                }
+                cb = ce;
+                if (c + 1 < c1) consumer_sync(nc);
+                continue;
+            }
             for (int32_t r0 = cb + tid; r0 < ce; r0 += E * nc) {
                 uint32_t uv[E];
                 EdgeVal e[E];
