@@ -67,6 +67,10 @@ def _load():
         lib.orc_load_stats.argtypes = [i32, P, P]
         lib.orc_lowd_iterate_threads.restype = i32
         lib.orc_lowd_iterate_threads.argtypes = [i32, i64, P, P, P, P, i32, i32, i32, P, P, P]
+        lib.orc_star_update.restype = C.c_double
+        lib.orc_star_update.argtypes = [i32, P, P, P, P]
+        lib.orc_star_round.restype = i32
+        lib.orc_star_round.argtypes = [i32, P, P, P, P, P, P, P, P, P]
         lib.orc_level_colouring.restype = i32
         lib.orc_level_colouring.argtypes = [i32, i64, P, P, P]
         _lib = lib
@@ -222,6 +226,37 @@ class LowdState:
             raise RuntimeError("could not start the threads")
         self.iters += T
 
+    def iterate_hub_star(self, T: int, plain_order, steps):
+        """T hub-star passes (the hub-star block update): Algorithm 1 over the plain edges in
+        plain_order, then every star step of `steps` (hub_star_structure): each star of the
+        step is set to the exact minimiser of the sum of squared loads over its splits
+        (star_update), the stars of a step being vertex-disjoint."""
+        lib = _load()
+        po = _c(plain_order, np.int32)
+        hubs, beg, edges = [], [0], []
+        for st in steps:
+            for hub, es in st.items():
+                hubs.append(int(hub))
+                edges.extend(int(e) for e in es)
+                beg.append(len(edges))
+        hubs = np.asarray(hubs, np.int32)
+        beg = np.asarray(beg, np.int64)
+        edges = np.asarray(edges, np.int32)
+        for _ in range(int(T)):
+            if po.shape[0]:
+                sub_u = self.u[po]
+                sub_v = self.v[po]
+                fu = self.fu[po].copy()
+                fv = self.fv[po].copy()
+                lib.orc_lowd_iterate(self.n, po.shape[0], _p(sub_u), _p(sub_v), None, 1,
+                                     _p(fu), _p(fv), _p(self.l), None)
+                self.fu[po] = fu
+                self.fv[po] = fv
+            if hubs.shape[0] and lib.orc_star_round(int(hubs.shape[0]), _p(hubs), _p(beg), _p(edges), _p(self.u),
+                                                    _p(self.v), _p(self.w), _p(self.fu), _p(self.fv), _p(self.l)):
+                raise MemoryError
+        self.iters += T
+
     def stats(self):
         """(sum l, sum l^2, max l)."""
         lib = _load()
@@ -284,6 +319,57 @@ def level_order(n, u, v):
     order = np.argsort(colour, kind="stable").astype(np.int32)
     offs = np.searchsorted(colour[order], np.arange(C + 1)).astype(np.int64)
     return order, offs, colour
+
+
+def star_update(lh, l, w, t):
+    """Exact minimisation of the sum of squared loads over the splits of one star (hub load
+    lh, leaf loads l[j], edge weights w[j], t[j] = the hub's share f_e(h)), all other splits
+    fixed: water filling, t_j = clip(B_j + w_j - lam, 0, w_j) with lam the hub's new load
+    (lowd_oracle.c, orc_star_update).  Returns (lh, l, t, lam).
+
+    Parity pinned by tests/test_oracle_stars.py: the KKT conditions of the star's quadratic
+    program (interior shares leave the leaf at the hub's load, clipped ones on the right
+    side of it); a one-leaf star equals Algorithm 1's edge update; many sequential passes of
+    Algorithm 1 over the star's edges converge to the same loads."""
+    lib = _load()
+    l = _c(l, np.float64).copy()
+    w = _c(w, np.float64)
+    t = _c(t, np.float64).copy()
+    lhv = np.array([lh], np.float64)
+    lam = lib.orc_star_update(int(l.shape[0]), _p(lhv), _p(l), _p(w), _p(t))
+    return float(lhv[0]), l, t, float(lam)
+
+
+def hub_star_structure(n, u, v, tau: int):
+    """The blocks of a hub-star pass, from their definition.  Hubs are the nodes of
+    (unweighted) degree >= tau.  An edge with exactly one hub end is a star edge; every other
+    edge is plain.  A leaf's star edges, ordered by its hub's degree (descending) then id,
+    go to steps 0, 1, 2, ...; in step k the star edges grouped by hub form vertex-disjoint
+    stars (one edge per leaf per step, hubs only as centres).  Returns (plain edge ids
+    ascending, steps: list over k of dict hub -> array of star edge ids, ascending)."""
+    u = np.asarray(u, np.int64)
+    v = np.asarray(v, np.int64)
+    m = u.shape[0]
+    deg = np.bincount(u, minlength=n) + np.bincount(v, minlength=n)
+    hub = deg >= tau
+    star = hub[u] ^ hub[v]
+    plain = np.nonzero(~star)[0].astype(np.int32)
+    se = np.nonzero(star)[0]
+    h = np.where(hub[u[se]], u[se], v[se])
+    x = np.where(hub[u[se]], v[se], u[se])
+    o = np.lexsort((h, -deg[h], x))            # by leaf, then hub degree desc, then hub id
+    se, h, x = se[o], h[o], x[o]
+    first = np.searchsorted(x, x, side="left")
+    step = np.arange(se.shape[0]) - first
+    steps = []
+    for k in range(int(step.max()) + 1 if se.shape[0] else 0):
+        sel = step == k
+        hk, ek = h[sel], se[sel]
+        d = {}
+        for hh in np.unique(hk):
+            d[int(hh)] = np.sort(ek[hk == hh]).astype(np.int32)
+        steps.append(d)
+    return plain, steps
 
 
 def extract(n, u, v, wu, loads):
@@ -386,3 +472,14 @@ def solve(n, u, v, w=None, T: int = 100, prune_first: bool = True, order=None):
     return dict(prune=pr, n_H=nh, u_H=uh, v_H=vh, w_H=wh, map=idmap, state=st,
                 S=idmap[S], W=Wb, k=int(S.shape[0]), scale=scale,
                 rho=(Wb / scale / S.shape[0]) if S.shape[0] else 0.0)
+
+
+def auto_hub_threshold(n, u, v):
+    """The automatic hub threshold of the hub-star pass: the smallest power of two 2^k
+    (k >= 1) such that at most 2^(k-1) nodes have (unweighted) degree >= 2^k (so at most
+    half as many hubs as the threshold).  Returns an int (2^30 if no k up to 30 qualifies)."""
+    deg = np.bincount(np.asarray(u, np.int64), minlength=n) + np.bincount(np.asarray(v, np.int64), minlength=n)
+    for k in range(1, 31):
+        if int((deg >= (1 << k)).sum()) <= (1 << (k - 1)):
+            return 1 << k
+    return 1 << 30

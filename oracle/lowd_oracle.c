@@ -24,6 +24,9 @@
  *   orc_extract        argsort by load, peel lowest, best prefix        [Alg. 1 extraction]
  *   orc_level_colouring  pass order for graphs of any size (conflict-free batches; the
  *                      paper visits edges in any order, Fig. 1 caption)
+ *   orc_star_update    exact minimiser of sum l^2 over one star's splits (the local
+ *                      optimality of Sec. III-C over a block of edges)
+ *   orc_star_round     star updates over a list of stars, in order
  *   orc_greedy         Charikar peeling (test-only cross-check)         [Alg. 3]
  *   orc_densest_flow   exact rho* and maximal densest set by min cut    [Sec. I, Goldberg]
  *   orc_ldd            exact locally-dense decomposition by min cuts    [Sec. II, Def. LDD]
@@ -682,3 +685,116 @@ int32_t orc_level_colouring(int32_t n, int64_t m, const int32_t* u, const int32_
     return C;
 }
 
+
+/* ------------------------------------------------------------------ hub-star block update */
+
+typedef struct { double x; int32_t kind; } breakpoint;
+
+static int cmp_breakpoint(const void* a, const void* b) {
+    const breakpoint* p = (const breakpoint*)a;
+    const breakpoint* q = (const breakpoint*)b;
+    if (p->x != q->x) return p->x < q->x ? -1 : 1;
+    return p->kind - q->kind;
+}
+
+/* Exact minimisation of the sum of squared loads over the splits of one star: hub h with
+ * leaves j = 0..q-1 joined by edges of weight w[j]; t[j] = f_e(h) on input and output.  With
+ * the other edges fixed, B_h = l_h - sum t and B_j = l_j - (w_j - t_j); the loads after are
+ * L_h = B_h + sum t_j and L_j = B_j + w_j - t_j.  Setting the gradient to zero with the box
+ * 0 <= t_j <= w_j gives t_j = clip(B_j + w_j - lam, 0, w_j) where lam = L_h solves
+ *     g(lam) = B_h + sum_j clip(B_j + w_j - lam, 0, w_j) - lam = 0,
+ * g strictly decreasing and piecewise linear with breakpoints B_j and B_j + w_j ("water
+ * filling").  The breakpoints are sorted and g is followed from the left until it changes
+ * sign; the root is then exact on that linear piece.  Updates lh, l[j] (loads of the leaves)
+ * and t; returns lam.  A star of one leaf is Algorithm 1's edge update. */
+double orc_star_update(int32_t q, double* lh, double* l, const double* w, double* t) {
+    if (q <= 0) return *lh;
+    breakpoint* bp = (breakpoint*)malloc(sizeof(breakpoint) * (size_t)(2 * q));
+    double Bh = *lh;
+    for (int32_t j = 0; j < q; ++j) Bh -= t[j];
+    /* g at lam = -inf side: every clip is w_j (lam below all B_j).  Walk the breakpoints in
+     * order: at B_j the term j starts falling with slope -1, at B_j + w_j it stops. */
+    double sumw = 0.0;
+    for (int32_t j = 0; j < q; ++j) {
+        const double Bj = l[j] - (w[j] - t[j]);
+        bp[2 * j].x = Bj;          bp[2 * j].kind = 0;   /* start of the falling piece */
+        bp[2 * j + 1].x = Bj + w[j]; bp[2 * j + 1].kind = 1;   /* end of it */
+        sumw += w[j];
+    }
+    qsort(bp, (size_t)(2 * q), sizeof(breakpoint), cmp_breakpoint);
+    /* on a piece, g(lam) = C - (1 + a) lam with a = number of falling terms and
+     * C = B_h + sum of w over terms left of their piece + sum of (B_j + w_j) over falling ones */
+    double C = Bh + sumw;
+    int32_t a = 0;
+    double lam = 0.0;
+    int found = 0;
+    double left = -INFINITY;
+    for (int32_t i = 0; i <= 2 * q && !found; ++i) {
+        const double right = i < 2 * q ? bp[i].x : INFINITY;
+        /* root of C - (1 + a) lam on [left, right] */
+        const double r = C / (double)(1 + a);
+        if (r <= right && r >= left) { lam = r; found = 1; break; }
+        if (i == 2 * q) break;
+        if (bp[i].kind == 0) {   /* term enters its falling piece: C += B_j + w_j - w_j = B_j */
+            C += bp[i].x - 0.0;   /* adds (B_j + w_j) and removes w_j: net B_j */
+            a += 1;
+        } else {                 /* term leaves it: C -= (B_j + w_j) */
+            C -= bp[i].x;
+            a -= 1;
+        }
+        left = right;
+    }
+    if (!found) lam = C / (double)(1 + a);
+    double Lh = Bh;
+    for (int32_t j = 0; j < q; ++j) {
+        const double Bj = l[j] - (w[j] - t[j]);
+        double tj = Bj + w[j] - lam;
+        if (tj < 0.0) tj = 0.0;
+        if (tj > w[j]) tj = w[j];
+        t[j] = tj;
+        l[j] = Bj + w[j] - tj;
+        Lh += tj;
+    }
+    *lh = Lh;
+    free(bp);
+    return lam;
+}
+
+/* One round of star updates: stars s = 0..ns-1 in order (all stars of step 0, then of step
+ * 1, ...), star s = hub star_hub[s] with the edges star_edge[beg[s] .. beg[s+1]).  Each is set
+ * by orc_star_update from the current loads and splits (fu/fv the shares of u/v).  Returns 0,
+ * or -1 if scratch could not be allocated (nothing changed then). */
+int32_t orc_star_round(int32_t ns, const int32_t* star_hub, const int64_t* beg, const int32_t* star_edge,
+                       const int32_t* u, const int32_t* v, const double* w, double* fu, double* fv, double* l) {
+    int64_t qmax = 0;
+    for (int32_t s = 0; s < ns; ++s)
+        if (beg[s + 1] - beg[s] > qmax) qmax = beg[s + 1] - beg[s];
+    double* ll = (double*)malloc(sizeof(double) * (size_t)(qmax > 0 ? qmax : 1));
+    double* ww = (double*)malloc(sizeof(double) * (size_t)(qmax > 0 ? qmax : 1));
+    double* tt = (double*)malloc(sizeof(double) * (size_t)(qmax > 0 ? qmax : 1));
+    if (!ll || !ww || !tt) { free(ll); free(ww); free(tt); return -1; }
+    for (int32_t s = 0; s < ns; ++s) {
+        const int32_t hub = star_hub[s];
+        const int64_t b = beg[s];
+        const int32_t q = (int32_t)(beg[s + 1] - b);
+        for (int32_t j = 0; j < q; ++j) {
+            const int32_t e = star_edge[b + j];
+            const int hub_is_u = u[e] == hub;
+            ll[j] = l[hub_is_u ? v[e] : u[e]];
+            ww[j] = w ? w[e] : 1.0;
+            tt[j] = hub_is_u ? fu[e] : fv[e];
+        }
+        double lh = l[hub];
+        orc_star_update(q, &lh, ll, ww, tt);
+        l[hub] = lh;
+        for (int32_t j = 0; j < q; ++j) {
+            const int32_t e = star_edge[b + j];
+            const int hub_is_u = u[e] == hub;
+            l[hub_is_u ? v[e] : u[e]] = ll[j];
+            if (hub_is_u) { fu[e] = tt[j]; fv[e] = ww[j] - tt[j]; }
+            else { fv[e] = tt[j]; fu[e] = ww[j] - tt[j]; }
+        }
+    }
+    free(ll); free(ww); free(tt);
+    return 0;
+}
