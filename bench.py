@@ -578,6 +578,24 @@ def main():
             pkg.lowd_free(h)
             pkg.lowd_mpnn_free(net)
 
+        # the same with hub-star block updates (automatic threshold): per pass Algorithm 1 over
+        # the plain edges, then every star's exact Sigma l^2 minimiser, from the equal split
+        h = pkg.lowd_load_graph(g.n, du, dv, dw, stream=stream)
+        t_a.record(stream)
+        pkg.lowd_prune(h)
+        st_s = pkg.lowd_iterate(h, args.rho_max_passes, check_every=check, rel_tol=1e-6, hub_stars=1)
+        t_b.record(stream)
+        t_b.synchronize()
+        info_s = pkg.lowd_get_info(h)
+        time_to_rho_stars = {"rel_gap": 1e-6, "converged": bool(st_s["converged"]),
+                             "passes": int(st_s["iters_done"]), "ms": t_a.elapsed_time(t_b),
+                             "check_every": check, "rho": st_s["rho_best"], "D": st_s["max_load"],
+                             "star_threshold": info_s["star_threshold"], "star_steps": info_s["star_steps"],
+                             "stars": info_s["stars"], "star_edges": info_s["star_edges"],
+                             "plain_classes": info_s["classes"] - info_s["star_steps"],
+                             "includes": "prune + star structure + colouring + passes + FP64 checks"}
+        pkg.lowd_free(h)
+
         # end to end through the C ABI with pinned host buffers (copies inside the timing)
         hu = torch.from_numpy(g.u).pin_memory().numpy()
         hv = torch.from_numpy(g.v).pin_memory().numpy()
@@ -643,6 +661,7 @@ def main():
         "stages_ms": stages,
         "time_to_rho": time_to_rho,
         "time_to_rho_warm_start": time_to_rho_warm,
+        "time_to_rho_hub_stars": time_to_rho_stars,
         "gpu_launches": int(launches),
         "gpu_launches_per_step": int(launches // max(args.steps, 1)),
         "clocks": ck,

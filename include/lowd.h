@@ -81,6 +81,24 @@ typedef struct {
                              for the previous updates of its two nodes); same pass as kernel 1.
                              Default 0 (kernel 1: on dense cores whose hubs appear in every
                              class it is faster, as waiting warps sleep at the barrier) */
+    int32_t hub_stars;    /* hub-star block updates (read when the schedule is built, i.e. by
+                             the first lowd_iterate of a graph): 0 = off (default); 1 =
+                             automatic threshold; t >= 2 = threshold.  Nodes of (unweighted)
+                             degree >= t are hubs; an edge with exactly one hub end is a star
+                             edge.  A pass runs Algorithm 1 over the other edges in the
+                             schedule's own order of their subgraph (circle colouring or
+                             level order), then the star steps: the star edges of each leaf
+                             are ranked by hub degree (descending) then hub id, and step k
+                             holds every leaf's k-th star edge, grouped by hub into
+                             vertex-disjoint stars.  Each star's splits become the exact
+                             minimiser of the sum of squared loads over them, all else fixed
+                             (Sec. III-C's local optimality over a block of edges; a one-leaf
+                             star is Algorithm 1's update), so sum l^2 still never rises and
+                             the loads converge to the same optimum.  The automatic threshold
+                             is the smallest power of two 2^k (k >= 1) with at most 2^(k-1)
+                             nodes of degree >= 2^k.  lowd_get_edge_order then lists the plain
+                             classes, then one block per star step; lowd_info reports the
+                             threshold, steps, stars and star edges */
 } lowd_options;
 
 /* Statistics of the state after lowd_iterate (FP64, from loads re-derived from the
@@ -115,6 +133,10 @@ typedef struct {
                              global memory), 5 staged one-CTA sweep with pair loads and
                              per-node versions instead of class barriers */
     int32_t sweep_edges_per_thread; /* edges per consumer thread per class of kernel 1 */
+    int32_t star_threshold; /* hub degree threshold of the hub stars in use (0: none) */
+    int32_t star_steps;     /* star steps per pass (the last star_steps entries of classes) */
+    int32_t stars;          /* stars over all steps */
+    int64_t star_edges;     /* star edges (the rest, m - star_edges, run Algorithm 1) */
 } lowd_info;
 
 /*

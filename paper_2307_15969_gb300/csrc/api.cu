@@ -48,6 +48,7 @@ void free_all(lowd_ctx* h) {
     dfree(&h->cw); dfree(&h->cs); dfree(&h->l); dfree(&h->l_lo);
     dfree(&h->s2_ctab); dfree(&h->s2_beg); dfree(&h->s2_ea); dfree(&h->s2_eb);
     dfree(&h->s2_srcA); dfree(&h->s2_srcB); dfree(&h->s2_lp); dfree(&h->s2_blob); dfree(&h->s2_blobo);
+    dfree(&h->star_step_seg); dfree(&h->star_seg_beg); dfree(&h->star_seg_hub); dfree(&h->star_bbuf);
     dfree(&h->tmp); h->tmp_cap = 0;
     dfree(&h->d_stats); dfree(&h->d_i64); dfree(&h->d_i32);
     if (h->h_pin) cudaFreeHost(h->h_pin);
@@ -206,9 +207,10 @@ lowd_status lowd_iterate(lowd_handle h, int32_t k, const lowd_options* opt, lowd
     LOWD_TRY(check_handle(h));
     if (k < 0) return LOWD_ERR_INVALID_ARG;
     if (opt && (opt->check_every < 0 || opt->rel_tol < 0 || opt->schedule < 0 || opt->schedule > 2 ||
-                opt->node_versions < 0 || opt->node_versions > 1))
+                opt->node_versions < 0 || opt->node_versions > 1 || opt->hub_stars < 0))
         return LOWD_ERR_INVALID_ARG;
     h->use_versions = opt ? opt->node_versions : 0;
+    if (!h->inited) h->hub_tau = opt ? opt->hub_stars : 0;
     if (!h->inited) LOWD_TRY(lowd_sweep_prepare(h, opt ? opt->schedule : 0, nullptr));
     return lowd_sweep_run(h, k, opt, st);
 }
@@ -313,12 +315,16 @@ lowd_status lowd_get_info(lowd_handle h, lowd_info* info) {
     x.duplicates = h->dup;
     x.weighted = h->weighted;
     x.pruned = h->pruned;
-    x.classes = h->C;
+    x.classes = h->C + h->star_S;
     x.schedule = h->sched;
     x.max_degree = h->max_deg;
     x.prune_rounds = h->prune_rounds;
     x.sweep_kernel = h->sweep_kernel;
     x.sweep_edges_per_thread = h->sweep_E;
+    x.star_threshold = h->star_tau;
+    x.star_steps = h->star_S;
+    x.stars = h->star_nseg;
+    x.star_edges = h->star_m;
     *info = x;
     return LOWD_OK;
 }
@@ -432,8 +438,8 @@ lowd_status lowd_get_edge_order(lowd_handle h, int32_t* perm, int32_t* class_off
         dfree(&d);
         LOWD_TRY(r);
     }
-    LOWD_TRY(to_caller(h, class_offsets, h->coff_real, (size_t)h->C + 1));
-    if (classes) *classes = h->C;
+    LOWD_TRY(to_caller(h, class_offsets, h->coff_real, (size_t)h->C + h->star_S + 1));
+    if (classes) *classes = h->C + h->star_S;
     return LOWD_OK;
 }
 

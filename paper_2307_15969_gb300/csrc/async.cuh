@@ -123,4 +123,35 @@ __device__ __forceinline__ bool consumer_sync_or(int nc, bool pred) {
 }
 
 
+constexpr uint32_t kGridSpins = 1u << 24;    // bounded waits: grid barrier (with 64 ns sleeps)
+
+// Grid barrier of a cooperative launch: arrive on a counter, the last block to arrive opens
+// the next generation (count and gen start at zero; the counter is back at zero after every
+// barrier, so later launches reuse the words).  Bounded: on expiry bit 1 of the error word
+// is set and false is returned.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks, int32_t* err) {
+    __syncthreads();
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            *count = 0;
+            __threadfence();
+            atomicAdd((unsigned*)gen, 1u);
+        } else {
+            uint32_t spins = 0;
+            while (*gen == g) {
+                if (++spins > kGridSpins) { ok = false; atomicOr(err, 2); break; }
+                if (spins > 4096) __nanosleep(64);   // poll fast at first, then back off
+            }
+        }
+        __threadfence();
+    }
+    __shared__ int okb;
+    if (threadIdx.x == 0) okb = ok ? 1 : 0;
+    __syncthreads();
+    return okb != 0;
+}
+
 }  // namespace lowd

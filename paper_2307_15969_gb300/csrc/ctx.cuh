@@ -79,6 +79,19 @@ struct lowd_ctx {
     float2* s2_lp = nullptr;      // [n + 1] loads as (hi, lo) pairs during the passes
     uint32_t* s2_blob = nullptr;  // per chunk: header, ends, read descriptors (, weights)
     int64_t* s2_blobo = nullptr;  // [NC + 1] word offsets of the chunk blobs
+    // hub stars (block updates of the edges with exactly one end of degree >= tau), both
+    // schedules: the star edges follow the plain ones, at positions [star_p0, star_p0 + star_m)
+    int32_t hub_tau = 0;              // asked for: 0 off, 1 automatic threshold, >= 2 the threshold
+    int32_t star_tau = 0;             // threshold in use (0: no star edges)
+    int32_t star_S = 0;               // star steps per pass
+    int32_t star_nseg = 0;            // stars over all steps
+    int32_t star_maxseg = 0;          // most stars in one step
+    int64_t star_m = 0;               // star edges
+    int64_t star_p0 = 0;              // position of the first star edge
+    int32_t* star_step_seg = nullptr; // [star_S + 1] first star of each step
+    int32_t* star_seg_beg = nullptr;  // [star_nseg + 1] position of each star's first edge
+    int32_t* star_seg_hub = nullptr;  // [star_nseg] hub of each star
+    double* star_bbuf = nullptr;      // [star_m] leaf baselines of stars too large for registers
 
     // scratch
     void* tmp = nullptr;
@@ -151,6 +164,21 @@ lowd_status lowd_sweep_rederive(lowd_ctx* h, double* stats3);
 lowd_status lowd_sweep_splits_canonical(lowd_ctx* h, float* out_dev);
 lowd_status lowd_sweep_load_canonical(lowd_ctx* h, const float* splits_dev);
 lowd_status lowd_sweep_edge_order(lowd_ctx* h, int32_t* out_dev);
+
+// stars.cu
+struct StarSplit {
+    int32_t tau = 0;              // threshold in use (0: all edges plain)
+    int64_t m_plain = 0, ms = 0;  // plain and star edges
+    int32_t* dfull = nullptr;     // [n] unweighted degrees
+    int32_t* pid = nullptr;       // [m_plain] plain edge ids (null: every edge is plain)
+    int32_t* sid = nullptr;       // [ms] star edge ids
+    int32_t* gu = nullptr;        // [m_plain] ends of the plain edges
+    int32_t* gv = nullptr;
+    void release();
+};
+lowd_status lowd_star_split(lowd_ctx* h, int32_t hub_tau, StarSplit* sp);
+lowd_status lowd_star_blocks(lowd_ctx* h, const StarSplit& sp, int64_t p0, int32_t C_plain, int64_t m_real_plain);
+cudaError_t lowd_star_pass(lowd_ctx* h);
 
 // stream.cu
 lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon);

@@ -1,0 +1,608 @@
+// Hub stars: a block update of Algorithm 1's objective over the edges between a hub and its
+// low-degree neighbours.
+//
+// Sec. III-C shows that Algorithm 1's edge update is the exact minimiser of the sum of
+// squared loads over one split with all other splits fixed, which is why sum l^2 falls
+// monotonically.  The same holds for any block of splits whose exact minimiser is cheap.  A
+// star (a hub h and leaves j_1..j_q, one edge each) is such a block: with B_h = l_h - sum t_j
+// (t_j the hub's share of edge j) and B_j = l_j - (w_j - t_j) the loads without the star,
+// the minimiser gives the hub the load lam solving
+//     g(lam) = B_h + sum_j clip(B_j + w_j - lam, 0, w_j) - lam = 0
+// and edge j the share t_j = clip(B_j + w_j - lam, 0, w_j) (water filling: every leaf whose
+// share is not clipped ends at the hub's load).  A one-leaf star is Algorithm 1's update.
+//
+// Structure.  Nodes of (unweighted) degree >= tau are hubs; an edge with exactly one hub end
+// is a star edge, every other edge is plain.  A leaf's star edges, ordered by hub degree
+// (descending) then hub id, go to steps 0, 1, 2, ...; within a step the star edges of one
+// hub form a star, and the stars of a step are vertex-disjoint (a leaf has one edge per
+// step, hubs are never leaves).  A pass runs Algorithm 1 over the plain edges (their own
+// schedule), then the steps in order, the stars of a step in parallel.  The automatic
+// threshold is the smallest power of two 2^k (k >= 1) with at most 2^(k-1) nodes of degree
+// >= 2^k.
+//
+// Execution.  One cooperative launch per pass runs every step; blocks take the stars of a
+// step, one star per block at a time, and meet at a bounded grid barrier between steps.  A
+// block keeps up to kStarRegs edges per thread in registers (the rest of a large star in an
+// FP64 scratch array) and solves g(lam) = 0 in FP64 inside a shrinking bracket, by Newton
+// steps and (when a Newton step leaves the bracket) Illinois secant steps (star_root); each
+// evaluation of g is one block reduction.  The new splits are rounded to FP32 and the loads
+// are computed from the rounded splits, so loads and splits stay consistent; loads are kept
+// as FP32 pairs (hi + lo) like in the pass kernels.
+#include "ctx.cuh"
+#include "prims.cuh"
+#include "async.cuh"
+
+#include <vector>
+
+using namespace lowd;
+
+namespace {
+
+constexpr int kT = 256;
+inline unsigned grid_for(int64_t n) { return lowd_grid_for(n, kT); }
+
+__global__ void k_star_degrees(const int32_t* __restrict__ u, const int32_t* __restrict__ v, int64_t m,
+                               int32_t* __restrict__ deg) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        atomicAdd(&deg[u[e]], 1);
+        atomicAdd(&deg[v[e]], 1);
+    }
+}
+
+// counts of nodes with degree >= 2^k, k = 0..30 (for the automatic threshold)
+__global__ void k_degree_powers(const int32_t* __restrict__ deg, int32_t n, unsigned long long* __restrict__ cnt) {
+    __shared__ unsigned long long c[32];
+    if (threadIdx.x < 32) c[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = deg[i];
+        for (int k = 0; k < 31 && d >= (1 << k); ++k) atomicAdd(&c[k], 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && c[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], c[threadIdx.x]);
+}
+
+__global__ void k_star_flags(const int32_t* __restrict__ u, const int32_t* __restrict__ v, int64_t m,
+                             const int32_t* __restrict__ deg, int32_t tau, int32_t* __restrict__ is_plain,
+                             int32_t* __restrict__ is_star) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const bool ha = deg[u[e]] >= tau, hb = deg[v[e]] >= tau;
+        is_star[e] = (ha != hb) ? 1 : 0;
+        is_plain[e] = (ha != hb) ? 0 : 1;
+    }
+}
+
+__global__ void k_select_ids(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t m,
+                             int32_t* __restrict__ ids) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        if (flag[e]) ids[pos[e]] = (int32_t)e;
+}
+
+__global__ void k_gather_ends(const int32_t* __restrict__ ids, int64_t k, const int32_t* __restrict__ u,
+                              const int32_t* __restrict__ v, int32_t* __restrict__ su, int32_t* __restrict__ sv) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        su[i] = u[ids[i]];
+        sv[i] = v[ids[i]];
+    }
+}
+
+// sort keys of the star edges order[i]: which 0 = hub id, 1 = inverted hub degree, 2 = leaf
+// id (three stable passes: leaf ascending, hub degree descending, hub id ascending)
+__global__ void k_star_keys(const int32_t* __restrict__ order, int64_t k, const int32_t* __restrict__ u,
+                            const int32_t* __restrict__ v, const int32_t* __restrict__ deg, int32_t tau, int which,
+                            uint32_t* __restrict__ key) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = order[i];
+        const bool ha = deg[u[e]] >= tau;
+        const int32_t hub = ha ? u[e] : v[e], leaf = ha ? v[e] : u[e];
+        key[i] = which == 0 ? (uint32_t)hub : (which == 1 ? 0x7fffffffu - (uint32_t)deg[hub] : (uint32_t)leaf);
+    }
+}
+
+// step of each star edge = its rank among its leaf's star edges (leafkey sorted): key (step, hub)
+__global__ void k_star_step_keys(const uint32_t* __restrict__ leafkey, const int32_t* __restrict__ order, int64_t k,
+                                 const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                                 const int32_t* __restrict__ deg, int32_t tau, uint64_t* __restrict__ key) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = leafkey[i];
+        int64_t lo = 0, hi = i;   // first entry of this leaf
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (leafkey[mid] < x) lo = mid + 1; else hi = mid;
+        }
+        const int32_t e = order[i];
+        const int32_t hub = deg[u[e]] >= tau ? u[e] : v[e];
+        key[i] = ((uint64_t)(i - lo) << 32) | (uint32_t)hub;
+    }
+}
+
+__global__ void k_star_heads(const uint64_t* __restrict__ key, int64_t k, int32_t* __restrict__ head) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+        head[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+}
+
+// per star (segment of equal (step, hub) keys): its first position and hub; per step its
+// first star
+__global__ void k_star_segments(const uint64_t* __restrict__ key, const int32_t* __restrict__ head,
+                                const int32_t* __restrict__ hpos, int64_t k, int32_t p0, int32_t* __restrict__ seg_beg,
+                                int32_t* __restrict__ seg_hub, int32_t* __restrict__ step_seg) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        if (!head[i]) continue;
+        const int32_t sg = hpos[i];
+        seg_beg[sg] = p0 + (int32_t)i;
+        seg_hub[sg] = (int32_t)(key[i] & 0xffffffffu);
+        const uint32_t stp = (uint32_t)(key[i] >> 32);
+        if (i == 0 || (uint32_t)(key[i - 1] >> 32) != stp) step_seg[stp] = sg;
+    }
+}
+
+__global__ void k_set_i32(int32_t* __restrict__ x, int32_t val) { *x = val; }
+
+// ------------------------------------------------------------------ the star steps
+
+constexpr int kStarThreads = 256;
+constexpr int kStarRegs = 4;       // edges per thread held in registers
+constexpr int kStarNewton = 64;    // iteration cap of the root search (bracketed, so it always ends)
+
+// where the ends and loads live: schedule 1 keeps packed 16-bit ends (lo | hi << 16) and the
+// loads as two arrays (hi, lo); schedule 2 keeps int32 ends and the loads as float2 pairs
+struct StarIO {
+    const uint32_t* cuv;
+    const int32_t* ea;
+    const int32_t* eb;
+    float* lhi;
+    float* llo;
+    float2* lp;
+};
+
+template <bool PACKED>
+__device__ __forceinline__ void star_ends(const StarIO& io, int32_t p, int32_t& a, int32_t& b) {
+    if (PACKED) {
+        const uint32_t x = __ldg(io.cuv + p);
+        a = (int32_t)(x & 0xffffu);
+        b = (int32_t)(x >> 16);
+    } else {
+        a = __ldg(io.ea + p);
+        b = __ldg(io.eb + p);
+    }
+}
+
+template <bool PACKED>
+__device__ __forceinline__ double star_load(const StarIO& io, int32_t x) {
+    if (PACKED) return (double)__ldcg(io.lhi + x) + (double)__ldcg(io.llo + x);
+    const float2 v = __ldcg(io.lp + x);
+    return (double)v.x + (double)v.y;
+}
+
+template <bool PACKED>
+__device__ __forceinline__ void star_store(const StarIO& io, int32_t x, double val) {
+    const float hi = (float)val;
+    const float lo = (float)(val - (double)hi);
+    if (PACKED) {
+        __stcg(io.lhi + x, hi);
+        __stcg(io.llo + x, lo);
+    } else {
+        __stcg(io.lp + x, make_float2(hi, lo));
+    }
+}
+
+// block-wide sums of N values (every thread gets the same totals, summed in the same order)
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N], double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) sh[N * wid + i] = v[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k)
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] += sh[N * k + i];
+}
+
+// piece of g that edge (B, w) is on at lam: 0 share clipped at 0, 1 interior, 2 clipped at w
+__device__ __forceinline__ int piece(double B, double w, double lam) {
+    return lam >= B + w ? 0 : (lam <= B ? 2 : 1);
+}
+
+__device__ __forceinline__ double share(double B, double w, double lam) { return fmin(fmax(B + w - lam, 0.0), w); }
+
+// The root search.  g(lam) = B_h - lam + sum_j share_j(lam) is strictly decreasing and
+// piecewise linear; the bracket [lo, hi] (g(lo) >= 0 >= g(hi)) starts at [B_h, B_h + sum w]
+// and shrinks at every evaluation.  The next point is a Newton step from the last point when
+// it falls inside the bracket, else the secant of the bracket ends (Illinois: the g value of
+// an end kept twice in a row is halved).  Exact stops: a Newton step that stays on the piece
+// it started from is the root; a bracket whose ends are on the same piece for every edge is
+// linear, and its secant is the root.
+struct RootSearch {
+    double Bh, lo, hi, glo, ghi, x, gx, Ax;
+    int side = 0, stuck = 0;
+};
+
+template <bool WEIGHTED, int R>
+struct StarEdges {
+    // sums over the star's edges: registers first, then the scratch array
+    const double* rB;
+    const double* rw;
+    const float* cw;
+    const double* Bbuf;
+    int32_t pr, p1, bbuf_p0, B;
+    template <class F>
+    __device__ __forceinline__ void each(F f) const {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (rw[r] > 0.0) f(rB[r], rw[r]);
+        for (int32_t p = pr + (int32_t)threadIdx.x; p < p1; p += B)
+            f(Bbuf[p - bbuf_p0], WEIGHTED ? (double)__ldg(cw + p) : 1.0);
+    }
+};
+
+template <class Edges>
+__device__ double star_root(const Edges& E, double Bh, double wsum, double lh, double* sh) {
+    RootSearch S;
+    S.Bh = Bh;
+    S.lo = Bh;
+    S.hi = Bh + wsum;
+    S.x = fmin(fmax(lh, S.lo), S.hi);
+    double Xb;
+    {   // first evaluation: g at both bracket ends and at the start point
+        double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        const double lo = S.lo, hi = S.hi, x = S.x;
+        E.each([&](double Bj, double w) {
+            v[0] += share(Bj, w, lo);
+            v[1] += share(Bj, w, hi);
+            v[2] += share(Bj, w, x);
+            const int px = piece(Bj, w, x);
+            v[3] += px == 1 ? 1.0 : 0.0;
+            v[4] += px != piece(Bj, w, lo) ? 1.0 : 0.0;
+            v[5] += px != piece(Bj, w, hi) ? 1.0 : 0.0;
+        });
+        block_sum<6>(v, sh);
+        S.glo = Bh - lo + v[0];
+        S.ghi = Bh - hi + v[1];
+        S.gx = Bh - x + v[2];
+        S.Ax = v[3];
+        if (S.gx == 0.0) return x;
+        if (S.gx > 0.0) { S.lo = x; S.glo = S.gx; Xb = v[5]; }
+        else { S.hi = x; S.ghi = S.gx; Xb = v[4]; }
+    }
+    for (int it = 0; it < kStarNewton; ++it) {
+        if (Xb == 0.0)   // g is linear on [lo, hi]
+            return S.glo == S.ghi ? S.lo : fmin(fmax(S.lo + S.glo * (S.hi - S.lo) / (S.glo - S.ghi), S.lo), S.hi);
+        double y = S.x + S.gx / (1.0 + S.Ax);
+        const bool newton = y > S.lo && y < S.hi;
+        if (!newton) {
+            double a = S.glo, b = S.ghi;
+            const double damp = ldexp(1.0, -S.stuck);
+            if (S.side == 1) b *= damp;
+            if (S.side == -1) a *= damp;
+            y = S.lo + a * (S.hi - S.lo) / (a - b);
+            if (!(y > S.lo && y < S.hi)) y = 0.5 * (S.lo + S.hi);
+            if (!(y > S.lo && y < S.hi)) return S.lo;   // the bracket is down to adjacent doubles
+        }
+        double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        const double lo = S.lo, hi = S.hi, x = S.x;
+        E.each([&](double Bj, double w) {
+            v[0] += share(Bj, w, y);
+            const int py = piece(Bj, w, y);
+            v[1] += py == 1 ? 1.0 : 0.0;
+            v[2] += py != piece(Bj, w, x) ? 1.0 : 0.0;
+            v[3] += py != piece(Bj, w, lo) ? 1.0 : 0.0;
+            v[4] += py != piece(Bj, w, hi) ? 1.0 : 0.0;
+        });
+        block_sum<5>(v, sh);
+        const double gy = Bh - y + v[0];
+        if (gy == 0.0 || (newton && v[2] == 0.0)) return y;
+        if (gy > 0.0) {
+            S.lo = y; S.glo = gy; Xb = v[4];
+            S.stuck = S.side == 1 ? S.stuck + 1 : 1;
+            S.side = 1;
+        } else {
+            S.hi = y; S.ghi = gy; Xb = v[3];
+            S.stuck = S.side == -1 ? S.stuck + 1 : 1;
+            S.side = -1;
+        }
+        S.x = y;
+        S.gx = gy;
+        S.Ax = v[1];
+    }
+    return S.x;
+}
+
+template <bool WEIGHTED, bool PACKED>
+__global__ void __launch_bounds__(kStarThreads)
+k_star_steps(int32_t S, const int32_t* __restrict__ step_seg, const int32_t* __restrict__ seg_beg,
+             const int32_t* __restrict__ seg_hub, StarIO io, const float* __restrict__ cw, float* __restrict__ cs,
+             double* __restrict__ Bbuf, int32_t bbuf_p0, unsigned* __restrict__ bar, int32_t* __restrict__ err) {
+    __shared__ double sh[6 * (kStarThreads / 32)];
+    constexpr int R = kStarRegs;
+    const int32_t B = (int32_t)blockDim.x;
+    for (int32_t k = 0; k < S; ++k) {
+        const int32_t g0 = __ldg(step_seg + k), g1 = __ldg(step_seg + k + 1);
+        for (int32_t sg = g0 + (int32_t)blockIdx.x; sg < g1; sg += (int32_t)gridDim.x) {
+            const int32_t h = __ldg(seg_hub + sg);
+            const int32_t p0 = __ldg(seg_beg + sg), p1 = __ldg(seg_beg + sg + 1);
+            const int32_t pr = p0 + R * B;   // positions from pr on keep their baseline in Bbuf
+            // baselines: B_j = l_j - (w_j - t_j); sums of the hub shares and the weights
+            double rB[R], rw[R];
+            double v3[3] = {0.0, 0.0, threadIdx.x == 0 ? star_load<PACKED>(io, h) : 0.0};
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int32_t p = p0 + (int32_t)threadIdx.x + r * B;
+                rB[r] = 0.0;
+                rw[r] = 0.0;   // w = 0 marks an empty register slot (weights are > 0)
+                if (p < p1) {
+                    int32_t a, b;
+                    star_ends<PACKED>(io, p, a, b);
+                    const double w = WEIGHTED ? (double)__ldg(cw + p) : 1.0;
+                    const double sv = (double)__ldcg(cs + p);
+                    const bool ha = a == h;
+                    const double t = ha ? sv : w - sv;
+                    rB[r] = star_load<PACKED>(io, ha ? b : a) - (w - t);
+                    rw[r] = w;
+                    v3[0] += t;
+                    v3[1] += w;
+                }
+            }
+            for (int32_t p = pr + (int32_t)threadIdx.x; p < p1; p += B) {
+                int32_t a, b;
+                star_ends<PACKED>(io, p, a, b);
+                const double w = WEIGHTED ? (double)__ldg(cw + p) : 1.0;
+                const double sv = (double)__ldcg(cs + p);
+                const bool ha = a == h;
+                const double t = ha ? sv : w - sv;
+                Bbuf[p - bbuf_p0] = star_load<PACKED>(io, ha ? b : a) - (w - t);
+                v3[0] += t;
+                v3[1] += w;
+            }
+            block_sum<3>(v3, sh);
+            const double lh = v3[2];
+            const double Bh = lh - v3[0];
+            const StarEdges<WEIGHTED, R> E{rB, rw, cw, Bbuf, pr, p1, bbuf_p0, B};
+            const double lam = star_root(E, Bh, v3[1], lh, sh);
+            // new splits (FP32) and the loads they give
+            double vt[1] = {0.0};
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int32_t p = p0 + (int32_t)threadIdx.x + r * B;
+                if (p < p1) {
+                    int32_t a, b;
+                    star_ends<PACKED>(io, p, a, b);
+                    const bool ha = a == h;
+                    const float wf = WEIGHTED ? __ldg(cw + p) : 1.0f;
+                    const double w = rw[r];
+                    const double t = share(rB[r], w, lam);
+                    const float snew = fminf(fmaxf(ha ? (float)t : (float)(w - t), 0.0f), wf);
+                    const double ta = ha ? (double)snew : w - (double)snew;
+                    __stcg(cs + p, snew);
+                    star_store<PACKED>(io, ha ? b : a, rB[r] + w - ta);
+                    vt[0] += ta;
+                }
+            }
+            for (int32_t p = pr + (int32_t)threadIdx.x; p < p1; p += B) {
+                int32_t a, b;
+                star_ends<PACKED>(io, p, a, b);
+                const bool ha = a == h;
+                const float wf = WEIGHTED ? __ldg(cw + p) : 1.0f;
+                const double w = (double)wf;
+                const double Bj = Bbuf[p - bbuf_p0];
+                const double t = share(Bj, w, lam);
+                const float snew = fminf(fmaxf(ha ? (float)t : (float)(w - t), 0.0f), wf);
+                const double ta = ha ? (double)snew : w - (double)snew;
+                __stcg(cs + p, snew);
+                star_store<PACKED>(io, ha ? b : a, Bj + w - ta);
+                vt[0] += ta;
+            }
+            block_sum<1>(vt, sh);
+            if (threadIdx.x == 0) star_store<PACKED>(io, h, Bh + vt[0]);
+        }
+        if (k + 1 < S && !grid_barrier(bar, bar + 1, gridDim.x, err)) return;
+    }
+}
+
+}  // namespace
+
+void StarSplit::release() {
+    dfree(&dfull);
+    dfree(&pid);
+    dfree(&sid);
+    dfree(&gu);
+    dfree(&gv);
+}
+
+// Classify the edges of the current graph for hub stars (hub_tau: 1 automatic, >= 2 the
+// threshold).  With no star edge the split is released and reports all edges plain.
+lowd_status lowd_star_split(lowd_ctx* h, int32_t hub_tau, StarSplit* sp) {
+    cudaStream_t st = h->st;
+    const int64_t m = h->m;
+    const int32_t n = h->n;
+    *sp = StarSplit();
+    sp->m_plain = m;
+    if (hub_tau <= 0 || m == 0) return LOWD_OK;
+    int32_t *fl[2] = {nullptr, nullptr}, *fp[2] = {nullptr, nullptr};
+    unsigned long long* cnt = nullptr;
+    lowd_status s = LOWD_OK;
+    do {
+        if ((s = h->need_tmp(lowd_sort_tmp_bytes(m + 2)))) break;
+        if ((s = dalloc(h, &sp->dfull, n))) break;
+        cudaMemsetAsync(sp->dfull, 0, sizeof(int32_t) * (size_t)n, st);
+        LOWD_LAUNCH(k_star_degrees, grid_for(m), kT, 0, st, h->u, h->v, m, sp->dfull);
+        int32_t tau = hub_tau;
+        if (tau == 1) {
+            if ((s = dalloc(h, &cnt, 32))) break;
+            cudaMemsetAsync(cnt, 0, 32 * sizeof(unsigned long long), st);
+            LOWD_LAUNCH(k_degree_powers, grid_for(n), kT, 0, st, sp->dfull, n, cnt);
+            unsigned long long hc[32];
+            cudaError_t e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) { s = h->fail(e); break; }
+            tau = 1 << 30;
+            for (int k = 1; k < 31; ++k)
+                if (hc[k] <= (1ull << (k - 1))) { tau = 1 << k; break; }
+        }
+        for (int i = 0; i < 2 && s == LOWD_OK; ++i) {
+            if ((s = dalloc(h, &fl[i], m))) break;
+            s = dalloc(h, &fp[i], m);
+        }
+        if (s) break;
+        LOWD_LAUNCH(k_star_flags, grid_for(m), kT, 0, st, h->u, h->v, m, sp->dfull, tau, fl[0], fl[1]);
+        scan_exclusive<int32_t>(fl[0], fp[0], m, h->d_i32 + 14, h->tmp, st);
+        scan_exclusive<int32_t>(fl[1], fp[1], m, h->d_i32 + 15, h->tmp, st);
+        int32_t cnts[2];
+        cudaError_t e = cudaMemcpyAsync(cnts, h->d_i32 + 14, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { s = h->fail(e); break; }
+        if (cnts[1] == 0) {   // no star edge: every edge is plain
+            sp->release();
+            sp->m_plain = m;
+            break;
+        }
+        sp->tau = tau;
+        sp->m_plain = cnts[0];
+        sp->ms = cnts[1];
+        if ((s = dalloc(h, &sp->pid, sp->m_plain))) break;
+        if ((s = dalloc(h, &sp->sid, sp->ms))) break;
+        if ((s = dalloc(h, &sp->gu, sp->m_plain))) break;
+        if ((s = dalloc(h, &sp->gv, sp->m_plain))) break;
+        LOWD_LAUNCH(k_select_ids, grid_for(m), kT, 0, st, fl[0], fp[0], m, sp->pid);
+        LOWD_LAUNCH(k_select_ids, grid_for(m), kT, 0, st, fl[1], fp[1], m, sp->sid);
+        if (sp->m_plain > 0)
+            LOWD_LAUNCH(k_gather_ends, grid_for(sp->m_plain), kT, 0, st, sp->pid, sp->m_plain, h->u, h->v, sp->gu,
+                        sp->gv);
+        if (cudaGetLastError() != cudaSuccess) s = h->fail(cudaGetLastError());
+    } while (0);
+    for (int i = 0; i < 2; ++i) { dfree(&fl[i]); dfree(&fp[i]); }
+    dfree(&cnt);
+    if (s) sp->release();
+    return s;
+}
+
+// The star steps of sp, placed at positions [p0, p0 + ms) of the class-major order: writes
+// h->perm there (allocated by the caller), builds the step and star tables, and extends the
+// exported class offsets (h->coff_real, C_plain + 1 entries over m_real_plain real positions)
+// by one block per step.
+lowd_status lowd_star_blocks(lowd_ctx* h, const StarSplit& sp, int64_t p0, int32_t C_plain, int64_t m_real_plain) {
+    cudaStream_t st = h->st;
+    const int64_t ms = sp.ms;
+    const int32_t n = h->n;
+    if (ms == 0) return LOWD_OK;
+    uint32_t *sk0 = nullptr, *sk1 = nullptr;
+    int32_t *so0 = nullptr, *so1 = nullptr, *head = nullptr, *hpos = nullptr, *cnew = nullptr;
+    uint64_t *q0 = nullptr, *q1 = nullptr;
+    lowd_status s = LOWD_OK;
+    do {
+        if ((s = h->need_tmp(lowd_sort_tmp_bytes(ms + 2)))) break;
+        if ((s = dalloc(h, &sk0, ms)) || (s = dalloc(h, &sk1, ms)) || (s = dalloc(h, &so0, ms)) ||
+            (s = dalloc(h, &so1, ms)) || (s = dalloc(h, &head, ms)) || (s = dalloc(h, &hpos, ms)) ||
+            (s = dalloc(h, &q0, ms)) || (s = dalloc(h, &q1, ms)))
+            break;
+        cudaMemcpyAsync(so0, sp.sid, sizeof(int32_t) * (size_t)ms, cudaMemcpyDeviceToDevice, st);
+        int32_t* cur_o = so0;
+        int32_t* oth_o = so1;
+        const int nbits = bit_length_u64((uint64_t)(n > 1 ? n - 1 : 1));
+        for (int which = 0; which < 3; ++which) {   // hub, then hub degree (descending), then leaf
+            LOWD_LAUNCH(k_star_keys, grid_for(ms), kT, 0, st, cur_o, ms, h->u, h->v, sp.dfull, sp.tau, which, sk0);
+            const int c = radix_sort_pairs<uint32_t, int32_t>(sk0, cur_o, sk1, oth_o, ms, which == 1 ? 31 : nbits,
+                                                             h->tmp, st);
+            if (c) { int32_t* t = cur_o; cur_o = oth_o; oth_o = t; }
+            if (which == 2 && c) { uint32_t* t = sk0; sk0 = sk1; sk1 = t; }   // leaf keys in sk0
+        }
+        LOWD_LAUNCH(k_star_step_keys, grid_for(ms), kT, 0, st, sk0, cur_o, ms, h->u, h->v, sp.dfull, sp.tau, q0);
+        const int sbits = 32 + bit_length_u64((uint64_t)(h->max_deg > 0 ? h->max_deg : 1));   // step < max degree
+        const int cq = radix_sort_pairs<uint64_t, int32_t>(q0, cur_o, q1, oth_o, ms, sbits, h->tmp, st);
+        uint64_t* qk = cq ? q1 : q0;
+        int32_t* qo = cq ? oth_o : cur_o;
+        LOWD_LAUNCH(k_star_heads, grid_for(ms), kT, 0, st, qk, ms, head);
+        scan_exclusive<int32_t>(head, hpos, ms, h->d_i32 + 14, h->tmp, st);
+        int32_t NSg = 0;
+        uint64_t lastkey = 0;
+        cudaError_t e = cudaMemcpyAsync(&NSg, h->d_i32 + 14, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&lastkey, qk + ms - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { s = h->fail(e); break; }
+        const int32_t S = (int32_t)(lastkey >> 32) + 1;
+        if ((s = dalloc(h, &h->star_seg_beg, (size_t)NSg + 1)) || (s = dalloc(h, &h->star_seg_hub, (size_t)NSg)) ||
+            (s = dalloc(h, &h->star_step_seg, (size_t)S + 1)) || (s = dalloc(h, &h->star_bbuf, (size_t)ms)))
+            break;
+        LOWD_LAUNCH(k_star_segments, grid_for(ms), kT, 0, st, qk, head, hpos, ms, (int32_t)p0, h->star_seg_beg,
+                    h->star_seg_hub, h->star_step_seg);
+        LOWD_LAUNCH(k_set_i32, 1, 1, 0, st, h->star_seg_beg + NSg, (int32_t)(p0 + ms));
+        LOWD_LAUNCH(k_set_i32, 1, 1, 0, st, h->star_step_seg + S, NSg);
+        cudaMemcpyAsync(h->perm + p0, qo, sizeof(int32_t) * (size_t)ms, cudaMemcpyDeviceToDevice, st);
+        std::vector<int32_t> hs((size_t)S + 1), hb((size_t)NSg + 1);
+        e = cudaMemcpyAsync(hs.data(), h->star_step_seg, sizeof(int32_t) * hs.size(), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hb.data(), h->star_seg_beg, sizeof(int32_t) * hb.size(), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { s = h->fail(e); break; }
+        int32_t maxseg = 0;
+        for (int32_t k = 0; k < S; ++k) maxseg = hs[(size_t)k + 1] - hs[(size_t)k] > maxseg ? hs[(size_t)k + 1] - hs[(size_t)k] : maxseg;
+        // exported class offsets: the plain classes, then one block per star step
+        if ((s = dalloc(h, &cnew, (size_t)C_plain + S + 1))) break;
+        cudaMemcpyAsync(cnew, h->coff_real, sizeof(int32_t) * ((size_t)C_plain + 1), cudaMemcpyDeviceToDevice, st);
+        std::vector<int32_t> tail((size_t)S);
+        for (int32_t k = 1; k <= S; ++k)
+            tail[(size_t)k - 1] = (int32_t)(m_real_plain + (hb[(size_t)hs[(size_t)k]] - p0));
+        cudaMemcpyAsync(cnew + C_plain + 1, tail.data(), sizeof(int32_t) * tail.size(), cudaMemcpyHostToDevice, st);
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { s = h->fail(e); break; }
+        dfree(&h->coff_real);
+        h->coff_real = cnew;
+        cnew = nullptr;
+        h->star_tau = sp.tau;
+        h->star_S = S;
+        h->star_nseg = NSg;
+        h->star_m = ms;
+        h->star_p0 = p0;
+        h->star_maxseg = maxseg;
+        if (cudaGetLastError() != cudaSuccess) s = h->fail(cudaGetLastError());
+    } while (0);
+    dfree(&sk0); dfree(&sk1); dfree(&so0); dfree(&so1); dfree(&head); dfree(&hpos); dfree(&q0); dfree(&q1);
+    dfree(&cnew);
+    return s;
+}
+
+// One pass's star steps (one cooperative launch).  The grid barrier words (d_i32[12..13])
+// must be zero before the first launch of a run.
+cudaError_t lowd_star_pass(lowd_ctx* h) {
+    if (h->star_S <= 0) return cudaSuccess;
+    const bool weighted = h->cw != nullptr;
+    const bool packed = h->sched == 1;
+    auto kern = weighted ? (packed ? k_star_steps<true, true> : k_star_steps<true, false>)
+                         : (packed ? k_star_steps<false, true> : k_star_steps<false, false>);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kStarThreads, 0);
+    if (e != cudaSuccess) return e;
+    int blocks = lowd_device_sms() * (per_sm >= 2 ? 2 : 1);
+    if (h->star_maxseg < blocks) blocks = h->star_maxseg > 0 ? h->star_maxseg : 1;
+    StarIO io{};
+    if (packed) {
+        io.cuv = h->cuv;
+        io.lhi = h->l;
+        io.llo = h->l_lo;
+    } else {
+        io.ea = h->s2_ea;
+        io.eb = h->s2_eb;
+        io.lp = h->s2_lp;
+    }
+    int32_t S = h->star_S;
+    const int32_t* ss = h->star_step_seg;
+    const int32_t* sb = h->star_seg_beg;
+    const int32_t* shb = h->star_seg_hub;
+    const float* pcw = h->cw;
+    float* pcs = h->cs;
+    double* pbb = h->star_bbuf;
+    int32_t bp0 = (int32_t)h->star_p0;
+    unsigned* bar = reinterpret_cast<unsigned*>(h->d_i32 + 12);
+    int32_t* errp = h->d_i32 + 8;
+    void* args[] = {&S, &ss, &sb, &shb, &io, &pcw, &pcs, &pbb, &bp0, &bar, &errp};
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kStarThreads), args, 0, h->st);
+    lowd_note_launch();
+    return e;
+}

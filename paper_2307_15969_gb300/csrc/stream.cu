@@ -128,35 +128,7 @@ __global__ void k_pending(const uint8_t* __restrict__ has_pred, int64_t m, int32
     }
 }
 
-constexpr uint32_t kGridSpins = 1u << 24;    // bounded waits: grid barrier (with 64 ns sleeps)
 constexpr uint32_t kSpinLimit = 1u << 22;    // bounded waits: mbarrier try_wait rounds
-
-// Grid barrier of a cooperative launch: arrive on a counter, the last block to arrive opens
-// the next generation.  Bounded: on expiry the error word is set and false is returned.
-__device__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks, int32_t* err) {
-    __syncthreads();
-    bool ok = true;
-    if (threadIdx.x == 0) {
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(count, 1u) == nblocks - 1) {
-            *count = 0;
-            __threadfence();
-            atomicAdd((unsigned*)gen, 1u);
-        } else {
-            uint32_t spins = 0;
-            while (*gen == g) {
-                if (++spins > kGridSpins) { ok = false; atomicOr(err, 2); break; }
-                if (spins > 4096) __nanosleep(64);   // poll fast at first, then back off
-            }
-        }
-        __threadfence();
-    }
-    __shared__ int okb;
-    if (threadIdx.x == 0) okb = ok ? 1 : 0;
-    __syncthreads();
-    return okb != 0;
-}
 
 // Kahn's algorithm by levels.  ctl: [0..2] frontier sizes (rotating), [4] barrier count,
 // [5] barrier generation, [6] level count out.  Frontier r lives in fr[r & 1].  While the
@@ -215,6 +187,11 @@ __global__ void k_level_heads(const uint32_t* __restrict__ key, int64_t m, int32
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x)
         if (i == 0 || key[i] != key[i - 1]) coff[key[i]] = (int32_t)i;
+}
+
+__global__ void k_map_ids(const int32_t* __restrict__ ids, int64_t k, int32_t* __restrict__ x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = ids[x[i]];
 }
 
 // ------------------------------------------------------------------ chunked stream
@@ -806,8 +783,11 @@ k_sweep_grid(int32_t K, const int32_t* __restrict__ coff, const int32_t* __restr
 // initial splits (equal split or the given canonical-order splits) and the loads.
 lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
     cudaStream_t st = h->st;
-    const int64_t m = h->m;
     const int32_t n = h->n;
+    StarSplit sp;                       // hub stars: the level order covers the plain edges
+    int64_t m = h->m;
+    const int32_t* cu = h->u;
+    const int32_t* cv = h->v;
     int32_t* deg = nullptr;
     uint32_t* k32[2] = {nullptr, nullptr};
     uint64_t* k64[2] = {nullptr, nullptr};
@@ -820,6 +800,7 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
     int32_t *rb = nullptr, *pb = nullptr;
     lowd_status s = LOWD_OK;
     auto cleanup = [&]() {
+        sp.release();
         dfree(&deg); dfree(&k32[0]); dfree(&k32[1]); dfree(&k64[0]); dfree(&k64[1]); dfree(&val[0]);
         dfree(&val[1]); dfree(&succ); dfree(&pend); dfree(&level); dfree(&fr[0]); dfree(&fr[1]); dfree(&ctl);
         dfree(&has_pred); dfree(&okey[0]); dfree(&okey[1]); dfree(&oval[0]); dfree(&oval[1]);
@@ -827,8 +808,17 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
     };
     const bool weighted = h->w != nullptr;
     do {
+        if ((s = h->need_tmp(lowd_sort_tmp_bytes(2 * (h->m > n ? h->m : n) + 2)))) break;
+        // ---- 0. hub stars: classify the edges, keep the plain ones for the level order
+        if ((s = lowd_star_split(h, h->hub_tau, &sp))) break;
+        const int32_t* pid = sp.pid;
+        const int64_t ms = sp.ms;
+        if (pid) {
+            m = sp.m_plain;
+            cu = sp.gu;
+            cv = sp.gv;
+        }
         // ---- 1. key order: stable sort by tie hash, then by degree key
-        if ((s = h->need_tmp(lowd_sort_tmp_bytes(2 * (m > n ? m : n) + 2)))) break;
         if ((s = dalloc(h, &deg, n))) break;
         if ((s = dalloc(h, &val[0], 2 * m))) break;
         if ((s = dalloc(h, &val[1], 2 * m))) break;
@@ -841,18 +831,18 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
             if ((s = dalloc(h, &k64[0], m))) break;
             if ((s = dalloc(h, &k64[1], m))) break;
             cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)n, st);
-            LOWD_LAUNCH(k_count_degrees, grid_for(m), kT, 0, st, h->u, h->v, m, deg);
+            LOWD_LAUNCH(k_count_degrees, grid_for(m), kT, 0, st, cu, cv, m, deg);
             LOWD_LAUNCH(k_tie_keys, grid_for(m), kT, 0, st, m, k32[0], val[0]);
             int c1 = radix_sort_pairs<uint32_t, int32_t>(k32[0], val[0], k32[1], val[1], m, 32, h->tmp, st);
             int32_t* vtie = val[c1];
             int32_t* vother = val[1 - c1];
-            LOWD_LAUNCH(k_degree_keys, grid_for(m), kT, 0, st, vtie, m, h->u, h->v, deg, k64[0]);
+            LOWD_LAUNCH(k_degree_keys, grid_for(m), kT, 0, st, vtie, m, cu, cv, deg, k64[0]);
             const int dbits = bit_length_u64((uint64_t)(h->max_deg > 0 ? h->max_deg : 1));
             int c2 = radix_sort_pairs<uint64_t, int32_t>(k64[0], vtie, k64[1], vother, m, 32 + dbits, h->tmp, st);
             ord = c2 ? vother : vtie;
             int32_t* spare = c2 ? vtie : vother;
             // ---- 2. adjacency in key order, successors, pending counts
-            LOWD_LAUNCH(k_adj_entries, grid_for(m), kT, 0, st, ord, m, h->u, h->v, k32[0], spare);
+            LOWD_LAUNCH(k_adj_entries, grid_for(m), kT, 0, st, ord, m, cu, cv, k32[0], spare);
             // sort the 2m entries by node; `spare` (2m) holds the ranks, ping-pong with k32[1]
             int32_t* rk2 = nullptr;
             if ((s = dalloc(h, &rk2, 2 * m))) break;
@@ -862,7 +852,7 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
             int32_t* rks = c3 ? rk2 : spare;
             if ((s = dalloc(h, &succ, 2 * m))) { dfree(&rk2); break; }
             if ((s = dalloc(h, &has_pred, 2 * m))) { dfree(&rk2); break; }
-            LOWD_LAUNCH(k_successors, grid_for(2 * m), kT, 0, st, nodes, rks, 2 * m, ord, h->u, succ, has_pred);
+            LOWD_LAUNCH(k_successors, grid_for(2 * m), kT, 0, st, nodes, rks, 2 * m, ord, cu, succ, has_pred);
             dfree(&rk2);
             // ord must survive: copy it out of the ping-pong buffers
             int32_t* ord_keep = nullptr;
@@ -905,6 +895,7 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
             const int lbits = bit_length_u64((uint64_t)(C > 1 ? C - 1 : 1));
             int c4 = radix_sort_pairs<uint32_t, int32_t>(k32[0], fr[0], k32[1], fr[1], m, lbits, h->tmp, st);
             order = c4 ? fr[1] : fr[0];
+            if (pid) LOWD_LAUNCH(k_map_ids, grid_for(m), kT, 0, st, pid, m, order);   // subset -> edge ids
             if ((s = dalloc(h, &h->coff_real, (size_t)C + 1))) break;
             LOWD_LAUNCH(k_level_heads, grid_for(m), kT, 0, st, c4 ? k32[1] : k32[0], m, h->coff_real);
             LOWD_LAUNCH(k_fill_i32s, 1, 32, 0, st, h->coff_real + C, (int64_t)1, (int32_t)m);
@@ -970,7 +961,8 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
         for (int32_t J = 0; J < NCp; ++J) pad_beg.push_back(ctab[(size_t)J * kHdrInts]);
         pad_beg.push_back((int32_t)pad);
         real_beg.push_back((int32_t)real);
-        const int64_t m_pad = pad;
+        const int64_t m_pad_plain = pad;       // the star edges follow the plain positions
+        const int64_t m_pad = pad + ms;
         h->m_pad = m_pad;
         h->s2_NC = NCp;
         h->s2_K = K;
@@ -985,7 +977,6 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
         cudaMemcpyAsync(h->s2_beg, pad_beg.data(), sizeof(int32_t) * pad_beg.size(), cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(rb, real_beg.data(), sizeof(int32_t) * real_beg.size(), cudaMemcpyHostToDevice, st);
         // ---- 6. padded stream
-        if ((s = dalloc(h, &h->perm, m_pad))) break;
         if ((s = dalloc(h, &h->s2_ea, m_pad))) break;
         if ((s = dalloc(h, &h->s2_eb, m_pad))) break;
         if ((s = dalloc(h, &h->s2_srcA, m_pad))) break;
@@ -995,29 +986,35 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
         if ((s = dalloc(h, &h->l, (size_t)n + 1))) break;
         if ((s = dalloc(h, &h->l_lo, (size_t)n + 1))) break;
         if ((s = dalloc(h, &h->s2_lp, (size_t)n + 1))) break;
+        // ---- 6b. star steps at positions [m_pad_plain, m_pad)
+        if ((s = dalloc(h, &h->perm, m_pad))) break;
+        if ((s = lowd_star_blocks(h, sp, m_pad_plain, C, m))) break;
         if (m_pad > 0) {
-            LOWD_LAUNCH(k_fill_i32s, grid_for(m_pad), kT, 0, st, h->perm, m_pad, -1);
-            LOWD_LAUNCH(k_pad_scatter, grid_for(m), kT, 0, st, order, m, m_grid, rb, h->s2_beg, NCp, h->perm);
+            if (m_pad_plain > 0) LOWD_LAUNCH(k_fill_i32s, grid_for(m_pad_plain), kT, 0, st, h->perm, m_pad_plain, -1);
+            if (m > 0) LOWD_LAUNCH(k_pad_scatter, grid_for(m), kT, 0, st, order, m, m_grid, rb, h->s2_beg, NCp, h->perm);
             LOWD_LAUNCH(k_stream_gather, grid_for(m_pad), kT, 0, st, h->perm, m_pad, n, h->u, h->v, h->w,
                         init_splits_canon, h->s2_ea, h->s2_eb, h->cw, h->cs);
             // ---- 7. descriptors from each node's occurrences (sorted by node, stable in position)
-            if ((s = h->need_tmp(lowd_sort_tmp_bytes(2 * m_pad)))) break;
-            if ((s = dalloc(h, &okey[0], 2 * m_pad))) break;
-            if ((s = dalloc(h, &okey[1], 2 * m_pad))) break;
-            if ((s = dalloc(h, &oval[0], 2 * m_pad))) break;
-            if ((s = dalloc(h, &oval[1], 2 * m_pad))) break;
+            const int64_t mp = m_pad_plain;
+            if ((s = h->need_tmp(lowd_sort_tmp_bytes(2 * mp + 2)))) break;
+            if ((s = dalloc(h, &okey[0], 2 * mp))) break;
+            if ((s = dalloc(h, &okey[1], 2 * mp))) break;
+            if ((s = dalloc(h, &oval[0], 2 * mp))) break;
+            if ((s = dalloc(h, &oval[1], 2 * mp))) break;
             if ((s = dalloc(h, &gfirst, n))) break;
             if ((s = dalloc(h, &glast, n))) break;
-            LOWD_LAUNCH(k_occurrences, grid_for(m_pad), kT, 0, st, h->perm, h->s2_ea, h->s2_eb, m_pad, grid_pad, n,
-                        okey[0], oval[0]);
-            const int nb1 = bit_length_u64((uint64_t)n);   // keys 0..n (n = padding)
-            int c5 = radix_sort_pairs<uint32_t, int64_t>(okey[0], oval[0], okey[1], oval[1], 2 * m_pad, nb1, h->tmp, st);
-            uint32_t* sk = okey[c5];
-            int64_t* sv = oval[c5];
-            LOWD_LAUNCH(k_group_bounds, grid_for(2 * m_pad), kT, 0, st, sk, 2 * m_pad, (uint32_t)n, gfirst, glast);
-            const StreamLayout L = stream_layout(E, weighted);
-            LOWD_LAUNCH(k_descriptors, grid_for(2 * m_pad), kT, 0, st, sk, sv, 2 * m_pad, (uint32_t)n, gfirst, glast,
-                        h->s2_beg, NCp, S, D, L, h->s2_srcA, h->s2_srcB);
+            if (mp > 0) {
+                LOWD_LAUNCH(k_occurrences, grid_for(mp), kT, 0, st, h->perm, h->s2_ea, h->s2_eb, mp, grid_pad, n,
+                            okey[0], oval[0]);
+                const int nb1 = bit_length_u64((uint64_t)n);   // keys 0..n (n = padding)
+                int c5 = radix_sort_pairs<uint32_t, int64_t>(okey[0], oval[0], okey[1], oval[1], 2 * mp, nb1, h->tmp, st);
+                uint32_t* sk = okey[c5];
+                int64_t* sv = oval[c5];
+                LOWD_LAUNCH(k_group_bounds, grid_for(2 * mp), kT, 0, st, sk, 2 * mp, (uint32_t)n, gfirst, glast);
+                const StreamLayout L = stream_layout(E, weighted);
+                LOWD_LAUNCH(k_descriptors, grid_for(2 * mp), kT, 0, st, sk, sv, 2 * mp, (uint32_t)n, gfirst, glast,
+                            h->s2_beg, NCp, S, D, L, h->s2_srcA, h->s2_srcB);
+            }
         }
         // ---- 8. chunk blobs (what the pass kernel copies per chunk)
         {
@@ -1029,9 +1026,9 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
             cudaMemcpyAsync(h->s2_blobo, bo.data(), sizeof(int64_t) * bo.size(), cudaMemcpyHostToDevice, st);
             LOWD_LAUNCH(k_blob_headers, grid_for((int64_t)NCp * kHdrInts), kT, 0, st, h->s2_ctab, h->s2_blobo, NCp,
                         h->s2_blob);
-            if (m_pad > grid_pad)
-                LOWD_LAUNCH(k_blob_data, grid_for(m_pad - grid_pad), kT, 0, st, h->s2_beg, h->s2_blobo, NCp, grid_pad,
-                            m_pad, h->s2_ea, h->s2_eb, h->s2_srcA, h->s2_srcB, h->cw, h->s2_blob);
+            if (m_pad_plain > grid_pad)
+                LOWD_LAUNCH(k_blob_data, grid_for(m_pad_plain - grid_pad), kT, 0, st, h->s2_beg, h->s2_blobo, NCp,
+                            grid_pad, m_pad_plain, h->s2_ea, h->s2_eb, h->s2_srcA, h->s2_srcB, h->cw, h->s2_blob);
         }
         if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
         cudaError_t e = cudaStreamSynchronize(st);
@@ -1071,7 +1068,29 @@ cudaError_t lowd_stream_passes(lowd_ctx* h, int32_t passes) {
         return cudaGetLastError();
     };
     cudaMemsetAsync(h->d_i32 + 12, 0, 2 * sizeof(int32_t), h->st);   // grid barrier words
-    if (h->s2_K == 0) {
+    unsigned* bar = reinterpret_cast<unsigned*>(h->d_i32 + 12);
+    int32_t* errp = h->d_i32 + 8;
+    if (h->star_S > 0) {
+        // per pass: the plain edges (grid steps, then the chunked tail), then the star steps
+        auto gk = weighted ? k_sweep_grid<true> : k_sweep_grid<false>;
+        int32_t K = h->s2_K;
+        const int32_t* coff = h->coff_real;
+        const int32_t* pea = h->s2_ea;
+        const int32_t* peb = h->s2_eb;
+        const float* pcw = h->cw;
+        float* pcs = h->cs;
+        float2* plp = h->s2_lp;
+        void* args[] = {&K, &coff, &pea, &peb, &pcw, &pcs, &plp, &bar, &errp};
+        for (int32_t t = 0; t < passes && e == cudaSuccess; ++t) {
+            if (K > 0) {
+                e = cudaLaunchCooperativeKernel((const void*)gk, dim3(lowd_device_sms()), dim3(kGridThreads), args, 0,
+                                                h->st);
+                lowd_note_launch();
+            }
+            if (e == cudaSuccess && h->s2_tail) e = stream_launch(1);
+            if (e == cudaSuccess) e = lowd_star_pass(h);
+        }
+    } else if (h->s2_K == 0) {
         const int32_t per = (int32_t)(0x7fffffff / h->s2_NC);
         for (int32_t done = 0; done < passes && e == cudaSuccess;) {
             const int32_t k = passes - done < per ? passes - done : per;
@@ -1091,8 +1110,6 @@ cudaError_t lowd_stream_passes(lowd_ctx* h, int32_t passes) {
         const float* pcw = h->cw;
         float* pcs = h->cs;
         float2* plp = h->s2_lp;
-        unsigned* bar = reinterpret_cast<unsigned*>(h->d_i32 + 12);
-        int32_t* errp = h->d_i32 + 8;
         void* args[] = {&K, &coff, &pea, &peb, &pcw, &pcs, &plp, &bar, &errp};
         for (int32_t t = 0; t < passes && e == cudaSuccess; ++t) {
             e = cudaLaunchCooperativeKernel((const void*)gk, dim3(blocks), dim3(kGridThreads), args, 0, h->st);

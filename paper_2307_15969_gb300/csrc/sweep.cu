@@ -99,6 +99,12 @@ __global__ void k_pad_sizes(const int32_t* __restrict__ coff_real, int32_t C, in
         pcnt[c] = (coff_real[c + 1] - coff_real[c] + 3) & ~3;
 }
 
+// x[i] = ids[x[i]]: indices into a subset of the edges -> edge ids
+__global__ void k_subset_to_ids(const int32_t* __restrict__ ids, int64_t k, int32_t* __restrict__ x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = ids[x[i]];
+}
+
 __global__ void k_fill_perm(int32_t* __restrict__ perm_pad, int64_t m_pad) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_pad;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -1011,7 +1017,14 @@ cudaError_t run_passes(lowd_ctx* h, int32_t passes) {
     cudaError_t e = cudaMemsetAsync(h->d_i32 + 8, 0, sizeof(int32_t), h->st);
     if (e != cudaSuccess) return e;
     if (h->sched == 2) return lowd_stream_passes(h, passes);
-    return h->cw ? launch_sweep<true>(h, passes) : launch_sweep<false>(h, passes);
+    if (h->star_S == 0) return h->cw ? launch_sweep<true>(h, passes) : launch_sweep<false>(h, passes);
+    // hub stars: per pass, the plain classes, then the star steps
+    e = cudaMemsetAsync(h->d_i32 + 12, 0, 2 * sizeof(int32_t), h->st);   // grid barrier words
+    for (int32_t t = 0; t < passes && e == cudaSuccess; ++t) {
+        if (h->C > 0) e = h->cw ? launch_sweep<true>(h, 1) : launch_sweep<false>(h, 1);
+        if (e == cudaSuccess) e = lowd_star_pass(h);
+    }
+    return e;
 }
 
 }  // namespace
@@ -1034,12 +1047,18 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
     uint64_t* key[2] = {nullptr, nullptr};
     int32_t* val[2] = {nullptr, nullptr};
     int32_t *head = nullptr, *hpos = nullptr, *pcnt = nullptr;
+    StarSplit sp;   // hub stars: the circle colouring covers the plain edges
     lowd_status s = LOWD_OK;
     auto cleanup = [&]() {
+        sp.release();
         dfree(&key[0]); dfree(&key[1]); dfree(&val[0]); dfree(&val[1]);
         dfree(&head); dfree(&hpos); dfree(&pcnt);
     };
     do {
+        if ((s = lowd_star_split(h, h->hub_tau, &sp))) break;
+        const int64_t mc = sp.pid ? sp.m_plain : m;   // edges the colouring covers
+        const int32_t* cu = sp.pid ? sp.gu : h->u;
+        const int32_t* cv = sp.pid ? sp.gv : h->v;
         if ((s = h->need_tmp(lowd_sort_tmp_bytes(m > n ? m : n)))) break;
         if ((s = dalloc(h, &key[0], m))) break;
         if ((s = dalloc(h, &key[1], m))) break;
@@ -1051,21 +1070,22 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
         int cur = 0;
         uint64_t* kfin = key[0];
         int32_t* vfin = val[0];
-        if (m > 0) {
-            LOWD_LAUNCH(k_circle_colour, grid_for(m), kT, 0, st, h->u, h->v, m, n, key[0], val[0]);
+        if (mc > 0) {
+            LOWD_LAUNCH(k_circle_colour, grid_for(mc), kT, 0, st, cu, cv, mc, n, key[0], val[0]);
             const uint32_t P = (uint32_t)(n + (n & 1)) - 1u;
             const int cbits = bit_length_u64(P > 0 ? P - 1 : 0);
-            cur = radix_sort_pairs<uint64_t, int32_t>(key[0], val[0], key[1], val[1], m, cbits + kBankBits + 1, h->tmp, st);
+            cur = radix_sort_pairs<uint64_t, int32_t>(key[0], val[0], key[1], val[1], mc, cbits + kBankBits + 1, h->tmp, st);
             uint64_t* kA = key[cur];
             int32_t* vA = val[cur];
             uint64_t* kB = key[1 - cur];
             int32_t* vB = val[1 - cur];
-            LOWD_LAUNCH(k_bank_rounds, grid_for(m), kT, 0, st, kA, m, kB);
-            const int r2 = radix_sort_pairs<uint64_t, int32_t>(kB, vA, kA, vB, m, cbits + kBankBits + 1 + kRankBits, h->tmp, st);
+            LOWD_LAUNCH(k_bank_rounds, grid_for(mc), kT, 0, st, kA, mc, kB);
+            const int r2 = radix_sort_pairs<uint64_t, int32_t>(kB, vA, kA, vB, mc, cbits + kBankBits + 1 + kRankBits, h->tmp, st);
             kfin = r2 ? kA : kB;
             vfin = r2 ? vB : vA;
-            LOWD_LAUNCH(k_class_heads, grid_for(m), kT, 0, st, kfin, m, kRankBits + kBankBits + 1, head);
-            scan_exclusive<int32_t>(head, hpos, m, h->d_i32 + 5, h->tmp, st);
+            if (sp.pid) LOWD_LAUNCH(k_subset_to_ids, grid_for(mc), kT, 0, st, sp.pid, mc, vfin);
+            LOWD_LAUNCH(k_class_heads, grid_for(mc), kT, 0, st, kfin, mc, kRankBits + kBankBits + 1, head);
+            scan_exclusive<int32_t>(head, hpos, mc, h->d_i32 + 5, h->tmp, st);
             if (cudaMemcpyAsync(h->h_pin, h->d_i32 + 5, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                 cudaStreamSynchronize(st) != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
             C = *(int32_t*)h->h_pin;
@@ -1075,8 +1095,8 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
         if ((s = dalloc(h, &h->coff_real, (size_t)C + 1))) break;
         if ((s = dalloc(h, &h->coff, (size_t)C + 1))) break;
         if ((s = dalloc(h, &pcnt, (size_t)C + 1))) break;
-        if (m > 0) {
-            LOWD_LAUNCH(k_class_offsets, grid_for(m), kT, 0, st, head, hpos, m, C, h->coff_real);
+        if (mc > 0) {
+            LOWD_LAUNCH(k_class_offsets, grid_for(mc), kT, 0, st, head, hpos, mc, C, h->coff_real);
             LOWD_LAUNCH(k_pad_sizes, grid_for(C), kT, 0, st, h->coff_real, C, pcnt);
             scan_exclusive<int32_t>(pcnt, h->coff, C, h->coff + C, h->tmp, st);
         } else {
@@ -1087,13 +1107,15 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
         if (!h->coff_h) { s = LOWD_ERR_OUT_OF_MEMORY; break; }
         if (cudaMemcpyAsync(h->coff_h, h->coff, sizeof(int32_t) * ((size_t)C + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
-        const int64_t m_pad = h->coff_h[C];
+        const int64_t m_pad_plain = h->coff_h[C];
+        const int64_t m_pad = m_pad_plain + sp.ms;   // the star edges follow the plain classes
         h->m_pad = m_pad;
         if ((s = dalloc(h, &h->perm, m_pad))) break;
         if (m_pad > 0) LOWD_LAUNCH(k_fill_perm, grid_for(m_pad), kT, 0, st, h->perm, m_pad);
-        if (m > 0)
-            LOWD_LAUNCH(k_scatter_padded, grid_for(m), kT, 0, st, vfin, head, hpos, h->coff_real, h->coff, m,
+        if (mc > 0)
+            LOWD_LAUNCH(k_scatter_padded, grid_for(mc), kT, 0, st, vfin, head, hpos, h->coff_real, h->coff, mc,
                         h->perm);
+        if ((s = lowd_star_blocks(h, sp, m_pad_plain, C, mc))) break;
         if ((s = dalloc(h, &h->cuv, m_pad))) break;
         if (h->w && (s = dalloc(h, &h->cw, m_pad))) break;
         if ((s = dalloc(h, &h->cs, m_pad))) break;
@@ -1104,21 +1126,23 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
                         init_splits_canon, h->cuv, h->cw, h->cs);
         // ranks of every end among its node's updates in the pass order (the staged sweep
         // without class barriers); node degrees must fit 15 bits
-        if (m_pad > 0 && h->max_deg < 0x7fff) {
+        // (plain classes only)
+        if (m_pad_plain > 0 && h->max_deg < 0x7fff) {
+            const int64_t mq = m_pad_plain;
             uint32_t* ok[2] = {nullptr, nullptr};
             int32_t* ov[2] = {nullptr, nullptr};
-            bool good = (s = h->need_tmp(lowd_sort_tmp_bytes(2 * m_pad))) == LOWD_OK;
-            good = good && (s = dalloc(h, &ok[0], 2 * m_pad)) == LOWD_OK;
-            good = good && (s = dalloc(h, &ok[1], 2 * m_pad)) == LOWD_OK;
-            good = good && (s = dalloc(h, &ov[0], 2 * m_pad)) == LOWD_OK;
-            good = good && (s = dalloc(h, &ov[1], 2 * m_pad)) == LOWD_OK;
-            good = good && (s = dalloc(h, &h->crk, m_pad)) == LOWD_OK;
+            bool good = (s = h->need_tmp(lowd_sort_tmp_bytes(2 * mq))) == LOWD_OK;
+            good = good && (s = dalloc(h, &ok[0], 2 * mq)) == LOWD_OK;
+            good = good && (s = dalloc(h, &ok[1], 2 * mq)) == LOWD_OK;
+            good = good && (s = dalloc(h, &ov[0], 2 * mq)) == LOWD_OK;
+            good = good && (s = dalloc(h, &ov[1], 2 * mq)) == LOWD_OK;
+            good = good && (s = dalloc(h, &h->crk, mq)) == LOWD_OK;
             if (good) {
-                cudaMemsetAsync(h->crk, 0, sizeof(uint32_t) * (size_t)m_pad, st);
-                LOWD_LAUNCH(k_occurrence_keys, grid_for(m_pad), kT, 0, st, h->cuv, m_pad, ok[0], ov[0]);
-                const int cur2 = radix_sort_pairs<uint32_t, int32_t>(ok[0], ov[0], ok[1], ov[1], 2 * m_pad,
+                cudaMemsetAsync(h->crk, 0, sizeof(uint32_t) * (size_t)mq, st);
+                LOWD_LAUNCH(k_occurrence_keys, grid_for(mq), kT, 0, st, h->cuv, mq, ok[0], ov[0]);
+                const int cur2 = radix_sort_pairs<uint32_t, int32_t>(ok[0], ov[0], ok[1], ov[1], 2 * mq,
                                                                      bit_length_u64((uint64_t)n), h->tmp, st);
-                LOWD_LAUNCH(k_occurrence_ranks, grid_for(2 * m_pad), kT, 0, st, ok[cur2], ov[cur2], 2 * m_pad,
+                LOWD_LAUNCH(k_occurrence_ranks, grid_for(2 * mq), kT, 0, st, ok[cur2], ov[cur2], 2 * mq,
                             (uint32_t)n, reinterpret_cast<uint16_t*>(h->crk));
                 cudaStreamSynchronize(st);
             }

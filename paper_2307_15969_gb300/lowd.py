@@ -51,7 +51,8 @@ LOWD_BATCH_ORDER_LARGEST_FIRST = 2
 
 class lowd_options(C.Structure):
     _fields_ = [("check_every", C.c_int32), ("rel_tol", C.c_double),
-                ("schedule", C.c_int32), ("rederive_every", C.c_int32), ("node_versions", C.c_int32)]
+                ("schedule", C.c_int32), ("rederive_every", C.c_int32), ("node_versions", C.c_int32),
+                ("hub_stars", C.c_int32)]
 
 
 class lowd_stats(C.Structure):
@@ -65,7 +66,8 @@ class lowd_info(C.Structure):
                 ("duplicates", C.c_int64), ("weighted", C.c_int32), ("pruned", C.c_int32),
                 ("classes", C.c_int32), ("schedule", C.c_int32), ("max_degree", C.c_int32),
                 ("prune_rounds", C.c_int32), ("sweep_kernel", C.c_int32),
-                ("sweep_edges_per_thread", C.c_int32)]
+                ("sweep_edges_per_thread", C.c_int32), ("star_threshold", C.c_int32),
+                ("star_steps", C.c_int32), ("stars", C.c_int32), ("star_edges", C.c_int64)]
 
 
 class lowd_batch_options(C.Structure):
@@ -276,10 +278,10 @@ def lowd_prune(h: Handle):
 
 def lowd_iterate(h: Handle, k: int, check_every: int = 0, rel_tol: float = 0.0,
                  schedule: int = 0, allow_not_converged: bool = True, rederive_every: int = 0,
-                 node_versions: bool = False) -> dict:
+                 node_versions: bool = False, hub_stars: int = 0) -> dict:
     """k LOWD passes; returns the lowd_stats fields as a dict (plus 'status')."""
     o = lowd_options(int(check_every), float(rel_tol), int(schedule), int(rederive_every),
-                     int(bool(node_versions)))
+                     int(bool(node_versions)), int(hub_stars))
     st = lowd_stats()
     s = load_library().lowd_iterate(h.ptr, int(k), C.byref(o), C.byref(st))
     if s != LOWD_OK and not (allow_not_converged and s == LOWD_ERR_NOT_CONVERGED):
