@@ -91,7 +91,7 @@ struct lowd_ctx {
     int32_t* star_step_seg = nullptr; // [star_S + 1] first star of each step
     int32_t* star_seg_beg = nullptr;  // [star_nseg + 1] position of each star's first edge
     int32_t* star_seg_hub = nullptr;  // [star_nseg] hub of each star
-    double* star_bbuf = nullptr;      // [star_m] leaf baselines of stars too large for registers
+    float2* star_bbuf = nullptr;      // [star_m] (a_j, t_j) of stars too large for registers
 
     // scratch
     void* tmp = nullptr;

@@ -22,12 +22,12 @@
 //
 // Execution.  One cooperative launch per pass runs every step; blocks take the stars of a
 // step, one star per block at a time, and meet at a bounded grid barrier between steps.  A
-// block keeps up to kStarRegs edges per thread in registers (the rest of a large star in an
-// FP64 scratch array) and solves g(lam) = 0 in FP64 inside a shrinking bracket, by Newton
-// steps and (when a Newton step leaves the bracket) Illinois secant steps (star_root); each
-// evaluation of g is one block reduction.  The new splits are rounded to FP32 and the loads
-// are computed from the rounded splits, so loads and splits stay consistent; loads are kept
-// as FP32 pairs (hi + lo) like in the pass kernels.
+// block keeps up to kStarRegs edges per thread in registers (the rest of a large star in a
+// scratch array) and solves g(lam) = 0 inside a shrinking bracket, by Newton steps and (when
+// a Newton step leaves the bracket) Illinois secant steps (star_root); each evaluation of g
+// is one block reduction.  The arithmetic is FP32 in the hub's frame and the loads move by
+// error-free transfers of the split changes (see "Arithmetic" below), so loads and splits
+// stay consistent; loads are kept as FP32 pairs (hi + lo) like in the pass kernels.
 #include "ctx.cuh"
 #include "prims.cuh"
 #include "async.cuh"
@@ -139,9 +139,20 @@ __global__ void k_star_segments(const uint64_t* __restrict__ key, const int32_t*
 __global__ void k_set_i32(int32_t* __restrict__ x, int32_t val) { *x = val; }
 
 // ------------------------------------------------------------------ the star steps
+//
+// Arithmetic.  FP64 runs at a small fraction of the FP32 rate on this GPU, so the star update
+// works in FP32 in the frame of the hub's current load lh: per edge a_j = (l_j - lh) + t_j
+// (= B_j + w_j - lh, the hub load at which the edge's share starts to fall) and the hub
+// shares t_j; in that frame g(d) = sum_j (share_j(d) - t_j) - d with share_j(d) =
+// clip(a_j - d, 0, w_j), d = lam - lh, whose terms are small near convergence.  The loads move
+// by error-free transfers: with s the stored split f_e(a), every load change of the star is
+// +-(s_new - s_old), split into an exact (hi, lo) pair by TwoSum, added to each leaf's pair
+// and summed (pairwise, by TwoSum) into the hub's change, so a load stays the exact sum of
+// what moved and the star conserves the total weight.
 
-constexpr int kStarThreads = 256;
-constexpr int kStarRegs = 4;       // edges per thread held in registers
+constexpr int kStarThreads = 512;
+constexpr int kStarWarps = kStarThreads / 32;
+constexpr int kStarRegs = 8;       // edges per thread held in registers
 constexpr int kStarNewton = 64;    // iteration cap of the root search (bracketed, so it always ends)
 
 // where the ends and loads live: schedule 1 keeps packed 16-bit ends (lo | hi << 16) and the
@@ -168,159 +179,212 @@ __device__ __forceinline__ void star_ends(const StarIO& io, int32_t p, int32_t& 
 }
 
 template <bool PACKED>
-__device__ __forceinline__ double star_load(const StarIO& io, int32_t x) {
-    if (PACKED) return (double)__ldcg(io.lhi + x) + (double)__ldcg(io.llo + x);
-    const float2 v = __ldcg(io.lp + x);
-    return (double)v.x + (double)v.y;
+__device__ __forceinline__ float2 star_load(const StarIO& io, int32_t x) {
+    if (PACKED) return make_float2(__ldcg(io.lhi + x), __ldcg(io.llo + x));
+    return __ldcg(io.lp + x);
 }
 
 template <bool PACKED>
-__device__ __forceinline__ void star_store(const StarIO& io, int32_t x, double val) {
-    const float hi = (float)val;
-    const float lo = (float)(val - (double)hi);
+__device__ __forceinline__ void star_store(const StarIO& io, int32_t x, float2 v) {
     if (PACKED) {
-        __stcg(io.lhi + x, hi);
-        __stcg(io.llo + x, lo);
+        __stcg(io.lhi + x, v.x);
+        __stcg(io.llo + x, v.y);
     } else {
-        __stcg(io.lp + x, make_float2(hi, lo));
+        __stcg(io.lp + x, v);
     }
 }
 
-// block-wide sums of N values (every thread gets the same totals, summed in the same order)
-template <int N>
-__device__ __forceinline__ void block_sum(double (&v)[N], double* sh) {
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// x += (hi + lo), x a load pair: both parts by error-free transfers into x.x, errors to x.y
+__device__ __forceinline__ void pair_add(float2& x, float hi, float lo) {
+    float t, e;
+    two_sum(x.x, hi, t, e);
+    x.x = t;
+    x.y += e + lo;
+    two_sum(x.x, x.y, t, e);   // renormalise
+    x.x = t;
+    x.y = e;
+}
+
+// x += y for (hi, lo) pairs (TwoSum of the high parts, low parts added)
+__device__ __forceinline__ void pair_acc(float& hi, float& lo, float yh, float yl) {
+    float s, e;
+    two_sum(hi, yh, s, e);
+    hi = s;
+    lo += e + yl;
+}
+
+// block-wide sums: NP (hi, lo) pairs (TwoSum at every addition), NF floats, NI ints; every
+// thread gets the same totals, summed in the same order
+template <int NP, int NF, int NI>
+__device__ __forceinline__ void block_sum(float2 (&pp)[NP], float (&f)[NF], int (&k)[NI], float* shf, int* shi) {
+    constexpr int NW = 2 * NP + NF;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+    for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+        for (int i = 0; i < NP; ++i) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, pp[i].x, o), l2 = __shfl_xor_sync(0xffffffffu, pp[i].y, o);
+            pair_acc(pp[i].x, pp[i].y, h2, l2);
+        }
+#pragma unroll
+        for (int i = 0; i < NF; ++i) f[i] += __shfl_xor_sync(0xffffffffu, f[i], o);
+#pragma unroll
+        for (int i = 0; i < NI; ++i) k[i] += __shfl_xor_sync(0xffffffffu, k[i], o);
+    }
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();
-    if (lane == 0)
+    if (lane == 0) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) sh[N * wid + i] = v[i];
+        for (int i = 0; i < NP; ++i) { shf[NW * wid + 2 * i] = pp[i].x; shf[NW * wid + 2 * i + 1] = pp[i].y; }
+#pragma unroll
+        for (int i = 0; i < NF; ++i) shf[NW * wid + 2 * NP + i] = f[i];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) shi[NI * wid + i] = k[i];
+    }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < N; ++i) v[i] = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k)
+    for (int i = 0; i < NP; ++i) pp[i] = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int i = 0; i < N; ++i) v[i] += sh[N * k + i];
+    for (int i = 0; i < NF; ++i) f[i] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) k[i] = 0;
+    for (int w = 0; w < kStarWarps; ++w) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) pair_acc(pp[i].x, pp[i].y, shf[NW * w + 2 * i], shf[NW * w + 2 * i + 1]);
+#pragma unroll
+        for (int i = 0; i < NF; ++i) f[i] += shf[NW * w + 2 * NP + i];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) k[i] += shi[NI * w + i];
+    }
 }
 
-// piece of g that edge (B, w) is on at lam: 0 share clipped at 0, 1 interior, 2 clipped at w
-__device__ __forceinline__ int piece(double B, double w, double lam) {
-    return lam >= B + w ? 0 : (lam <= B ? 2 : 1);
-}
+// piece of g that edge (a, w) is on at d: 0 share clipped at 0, 1 interior, 2 clipped at w
+__device__ __forceinline__ int piece(float a, float w, float d) { return d >= a ? 0 : (d <= a - w ? 2 : 1); }
 
-__device__ __forceinline__ double share(double B, double w, double lam) { return fmin(fmax(B + w - lam, 0.0), w); }
+__device__ __forceinline__ float share(float a, float w, float d) { return fminf(fmaxf(a - d, 0.0f), w); }
 
-// The root search.  g(lam) = B_h - lam + sum_j share_j(lam) is strictly decreasing and
-// piecewise linear; the bracket [lo, hi] (g(lo) >= 0 >= g(hi)) starts at [B_h, B_h + sum w]
-// and shrinks at every evaluation.  The next point is a Newton step from the last point when
-// it falls inside the bracket, else the secant of the bracket ends (Illinois: the g value of
-// an end kept twice in a row is halved).  Exact stops: a Newton step that stays on the piece
-// it started from is the root; a bracket whose ends are on the same piece for every edge is
-// linear, and its secant is the root.
-struct RootSearch {
-    double Bh, lo, hi, glo, ghi, x, gx, Ax;
-    int side = 0, stuck = 0;
-};
+// the hub's share of an edge from the stored split s = f_e(a)
+__device__ __forceinline__ float hub_share(bool ha, float s, float w) { return ha ? s : w - s; }
 
+// the star's edges: registers first (a_j, old split, weight, side bit), then the scratch
+// array (a_j, t_j) of large stars
 template <bool WEIGHTED, int R>
 struct StarEdges {
-    // sums over the star's edges: registers first, then the scratch array
-    const double* rB;
-    const double* rw;
+    const float* ra;
+    const float* rs;
+    const float* rw;
+    unsigned rha;
     const float* cw;
-    const double* Bbuf;
+    const float2* Bbuf;
     int32_t pr, p1, bbuf_p0, B;
     template <class F>
     __device__ __forceinline__ void each(F f) const {
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (rw[r] > 0.0) f(rB[r], rw[r]);
-        for (int32_t p = pr + (int32_t)threadIdx.x; p < p1; p += B)
-            f(Bbuf[p - bbuf_p0], WEIGHTED ? (double)__ldg(cw + p) : 1.0);
+            if (rw[r] > 0.0f) f(ra[r], hub_share((rha >> r) & 1u, rs[r], rw[r]), rw[r]);
+        for (int32_t p = pr + (int32_t)threadIdx.x; p < p1; p += B) {
+            const float2 at = Bbuf[p - bbuf_p0];
+            f(at.x, at.y, WEIGHTED ? __ldg(cw + p) : 1.0f);
+        }
     }
 };
 
+// The root search in the frame of a reference hub load: g(d) = sum_j (share_j(d) - t_j) -
+// off - d (off = the frame's offset from the hub's current load) is strictly decreasing and
+// piecewise linear, with its root inside [lo, hi].  The bracket shrinks at every evaluation.
+// The next point is a Newton step from the last point when it falls inside the bracket,
+// else the secant of the bracket ends once both have been evaluated (Illinois: the g value
+// of an end kept twice in a row is halved), else the midpoint.  Exact stops: a Newton step
+// that stays on the piece it started from is the root; a bracket whose ends are on the same
+// piece for every edge is linear, and its secant is the root.  Each evaluation is one block
+// reduction; sums of the terms are compensated (hi, lo) pairs.
 template <class Edges>
-__device__ double star_root(const Edges& E, double Bh, double wsum, double lh, double* sh) {
-    RootSearch S;
-    S.Bh = Bh;
-    S.lo = Bh;
-    S.hi = Bh + wsum;
-    S.x = fmin(fmax(lh, S.lo), S.hi);
-    double Xb;
-    {   // first evaluation: g at both bracket ends and at the start point
-        double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        const double lo = S.lo, hi = S.hi, x = S.x;
-        E.each([&](double Bj, double w) {
-            v[0] += share(Bj, w, lo);
-            v[1] += share(Bj, w, hi);
-            v[2] += share(Bj, w, x);
-            const int px = piece(Bj, w, x);
-            v[3] += px == 1 ? 1.0 : 0.0;
-            v[4] += px != piece(Bj, w, lo) ? 1.0 : 0.0;
-            v[5] += px != piece(Bj, w, hi) ? 1.0 : 0.0;
-        });
-        block_sum<6>(v, sh);
-        S.glo = Bh - lo + v[0];
-        S.ghi = Bh - hi + v[1];
-        S.gx = Bh - x + v[2];
-        S.Ax = v[3];
-        if (S.gx == 0.0) return x;
-        if (S.gx > 0.0) { S.lo = x; S.glo = S.gx; Xb = v[5]; }
-        else { S.hi = x; S.ghi = S.gx; Xb = v[4]; }
-    }
+__device__ float star_root(const Edges& E, float lo, float hi, float off, float g0, int A0, float* shf, int* shi) {
+    float glo = 0.0f, ghi = 0.0f;
+    bool klo = false, khi = false;
+    float x = 0.0f, gx = g0;
+    int Ax = A0;
+    if (gx == 0.0f) return 0.0f;
+    if (gx > 0.0f) { lo = 0.0f; glo = gx; klo = true; } else { hi = 0.0f; ghi = gx; khi = true; }
+    int Xb = 1, side = 0, stuck = 0;
     for (int it = 0; it < kStarNewton; ++it) {
-        if (Xb == 0.0)   // g is linear on [lo, hi]
-            return S.glo == S.ghi ? S.lo : fmin(fmax(S.lo + S.glo * (S.hi - S.lo) / (S.glo - S.ghi), S.lo), S.hi);
-        double y = S.x + S.gx / (1.0 + S.Ax);
-        const bool newton = y > S.lo && y < S.hi;
+        if (Xb == 0 && klo && khi)   // g is linear on [lo, hi]
+            return glo == ghi ? lo : fminf(fmaxf(lo + glo * (hi - lo) / (glo - ghi), lo), hi);
+        float y = x + gx / (1.0f + (float)Ax);
+        const bool newton = y > lo && y < hi;
         if (!newton) {
-            double a = S.glo, b = S.ghi;
-            const double damp = ldexp(1.0, -S.stuck);
-            if (S.side == 1) b *= damp;
-            if (S.side == -1) a *= damp;
-            y = S.lo + a * (S.hi - S.lo) / (a - b);
-            if (!(y > S.lo && y < S.hi)) y = 0.5 * (S.lo + S.hi);
-            if (!(y > S.lo && y < S.hi)) return S.lo;   // the bracket is down to adjacent doubles
+            y = 0.5f * (lo + hi);
+            if (klo && khi) {
+                float a = glo, b = ghi;
+                const float damp = ldexpf(1.0f, -stuck);
+                if (side == 1) b *= damp;
+                if (side == -1) a *= damp;
+                const float ys = lo + a * (hi - lo) / (a - b);
+                if (ys > lo && ys < hi) y = ys;
+            }
+            if (!(y > lo && y < hi)) return x;   // the bracket is down to adjacent floats
         }
-        double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        const double lo = S.lo, hi = S.hi, x = S.x;
-        E.each([&](double Bj, double w) {
-            v[0] += share(Bj, w, y);
-            const int py = piece(Bj, w, y);
-            v[1] += py == 1 ? 1.0 : 0.0;
-            v[2] += py != piece(Bj, w, x) ? 1.0 : 0.0;
-            v[3] += py != piece(Bj, w, lo) ? 1.0 : 0.0;
-            v[4] += py != piece(Bj, w, hi) ? 1.0 : 0.0;
+        float2 G[1] = {make_float2(0.0f, 0.0f)};
+        float fz[1] = {0.0f};
+        int k[4] = {0, 0, 0, 0};
+        E.each([&](float a, float t, float w) {
+            float h, l;
+            two_sum(share(a, w, y), -t, h, l);
+            pair_acc(G[0].x, G[0].y, h, l);
+            const int py = piece(a, w, y);
+            k[0] += py == 1;
+            k[1] += py != piece(a, w, x);
+            k[2] += py != piece(a, w, lo);
+            k[3] += py != piece(a, w, hi);
         });
-        block_sum<5>(v, sh);
-        const double gy = Bh - y + v[0];
-        if (gy == 0.0 || (newton && v[2] == 0.0)) return y;
-        if (gy > 0.0) {
-            S.lo = y; S.glo = gy; Xb = v[4];
-            S.stuck = S.side == 1 ? S.stuck + 1 : 1;
-            S.side = 1;
+        block_sum<1, 1, 4>(G, fz, k, shf, shi);
+        const float gy = ((G[0].x - off) + G[0].y) - y;
+        if (gy == 0.0f || (newton && k[1] == 0)) return y;
+        if (gy > 0.0f) {
+            lo = y; glo = gy; klo = true; Xb = k[3];
+            stuck = side == 1 ? stuck + 1 : 1;
+            side = 1;
         } else {
-            S.hi = y; S.ghi = gy; Xb = v[3];
-            S.stuck = S.side == -1 ? S.stuck + 1 : 1;
-            S.side = -1;
+            hi = y; ghi = gy; khi = true; Xb = k[2];
+            stuck = side == -1 ? stuck + 1 : 1;
+            side = -1;
         }
-        S.x = y;
-        S.gx = gy;
-        S.Ax = v[1];
+        x = y;
+        gx = gy;
+        Ax = k[0];
     }
-    return S.x;
+    return x;
 }
+
+// leaf update and the hub's share of it, for one edge: s_old -> s_new (stored split f_e(a))
+template <bool PACKED>
+__device__ __forceinline__ void star_apply(const StarIO& io, float* cs, int32_t p, bool ha, int32_t leaf,
+                                           float s_old, float s_new, float& hub_hi, float& hub_lo) {
+    float d, e;
+    two_sum(s_new, -s_old, d, e);   // s_new - s_old = d + e exactly
+    __stcg(cs + p, s_new);
+    float2 L = star_load<PACKED>(io, leaf);
+    // hub = a: the hub's share is s, the leaf's w - s; hub = b: the other way round
+    pair_add(L, ha ? -d : d, ha ? -e : e);
+    star_store<PACKED>(io, leaf, L);
+    pair_acc(hub_hi, hub_lo, ha ? d : -d, ha ? e : -e);
+}
+
+// a_j = (l_j - frame) + t_j for a leaf load pair l_j and a frame pair
+__device__ __forceinline__ float frame_level(float2 L, float2 F, float t) { return ((L.x - F.x) + (L.y - F.y)) + t; }
 
 template <bool WEIGHTED, bool PACKED>
 __global__ void __launch_bounds__(kStarThreads)
 k_star_steps(int32_t S, const int32_t* __restrict__ step_seg, const int32_t* __restrict__ seg_beg,
              const int32_t* __restrict__ seg_hub, StarIO io, const float* __restrict__ cw, float* __restrict__ cs,
-             double* __restrict__ Bbuf, int32_t bbuf_p0, unsigned* __restrict__ bar, int32_t* __restrict__ err) {
-    __shared__ double sh[6 * (kStarThreads / 32)];
+             float2* __restrict__ Bbuf, int32_t bbuf_p0, unsigned* __restrict__ bar, int32_t* __restrict__ err) {
+    __shared__ float shf[6 * kStarWarps];
+    __shared__ int shi[4 * kStarWarps];
     constexpr int R = kStarRegs;
     const int32_t B = (int32_t)blockDim.x;
     for (int32_t k = 0; k < S; ++k) {
@@ -328,79 +392,132 @@ k_star_steps(int32_t S, const int32_t* __restrict__ step_seg, const int32_t* __r
         for (int32_t sg = g0 + (int32_t)blockIdx.x; sg < g1; sg += (int32_t)gridDim.x) {
             const int32_t h = __ldg(seg_hub + sg);
             const int32_t p0 = __ldg(seg_beg + sg), p1 = __ldg(seg_beg + sg + 1);
-            const int32_t pr = p0 + R * B;   // positions from pr on keep their baseline in Bbuf
-            // baselines: B_j = l_j - (w_j - t_j); sums of the hub shares and the weights
-            double rB[R], rw[R];
-            double v3[3] = {0.0, 0.0, threadIdx.x == 0 ? star_load<PACKED>(io, h) : 0.0};
+            const int32_t pr = p0 + R * B;   // positions from pr on go through the scratch array
+            const float2 lh = star_load<PACKED>(io, h);
+            // per edge: a_j (frame lh), old split, weight, leaf, side
+            float ra[R], rw[R], rs[R];
+            int32_t rl[R];
+            unsigned rha = 0;
+            float2 gp[1] = {make_float2(0.0f, 0.0f)};   // g(0) + 0, compensated
+            float f2[2] = {0.0f, 0.0f};                 // T, W
+            int k1[1] = {0};                            // interior edges at d = 0
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int32_t p = p0 + (int32_t)threadIdx.x + r * B;
-                rB[r] = 0.0;
-                rw[r] = 0.0;   // w = 0 marks an empty register slot (weights are > 0)
+                rw[r] = 0.0f;   // w = 0 marks an empty register slot (weights are > 0)
+                ra[r] = 0.0f;
+                rs[r] = 0.0f;
+                rl[r] = -1;
                 if (p < p1) {
                     int32_t a, b;
                     star_ends<PACKED>(io, p, a, b);
-                    const double w = WEIGHTED ? (double)__ldg(cw + p) : 1.0;
-                    const double sv = (double)__ldcg(cs + p);
+                    const float w = WEIGHTED ? __ldg(cw + p) : 1.0f;
+                    const float sv = __ldcg(cs + p);
                     const bool ha = a == h;
-                    const double t = ha ? sv : w - sv;
-                    rB[r] = star_load<PACKED>(io, ha ? b : a) - (w - t);
+                    const int32_t leaf = ha ? b : a;
+                    const float t = hub_share(ha, sv, w);
+                    ra[r] = frame_level(star_load<PACKED>(io, leaf), lh, t);
                     rw[r] = w;
-                    v3[0] += t;
-                    v3[1] += w;
+                    rs[r] = sv;
+                    rl[r] = leaf;
+                    rha |= ha ? (1u << r) : 0u;
+                    f2[0] += t;
+                    f2[1] += w;
+                    float hh, ll;
+                    two_sum(share(ra[r], w, 0.0f), -t, hh, ll);
+                    pair_acc(gp[0].x, gp[0].y, hh, ll);
+                    k1[0] += piece(ra[r], w, 0.0f) == 1;
                 }
             }
             for (int32_t p = pr + (int32_t)threadIdx.x; p < p1; p += B) {
                 int32_t a, b;
                 star_ends<PACKED>(io, p, a, b);
-                const double w = WEIGHTED ? (double)__ldg(cw + p) : 1.0;
-                const double sv = (double)__ldcg(cs + p);
+                const float w = WEIGHTED ? __ldg(cw + p) : 1.0f;
+                const float sv = __ldcg(cs + p);
                 const bool ha = a == h;
-                const double t = ha ? sv : w - sv;
-                Bbuf[p - bbuf_p0] = star_load<PACKED>(io, ha ? b : a) - (w - t);
-                v3[0] += t;
-                v3[1] += w;
+                const float t = hub_share(ha, sv, w);
+                const float av = frame_level(star_load<PACKED>(io, ha ? b : a), lh, t);
+                Bbuf[p - bbuf_p0] = make_float2(av, t);
+                f2[0] += t;
+                f2[1] += w;
+                float hh, ll;
+                two_sum(share(av, w, 0.0f), -t, hh, ll);
+                pair_acc(gp[0].x, gp[0].y, hh, ll);
+                k1[0] += piece(av, w, 0.0f) == 1;
             }
-            block_sum<3>(v3, sh);
-            const double lh = v3[2];
-            const double Bh = lh - v3[0];
-            const StarEdges<WEIGHTED, R> E{rB, rw, cw, Bbuf, pr, p1, bbuf_p0, B};
-            const double lam = star_root(E, Bh, v3[1], lh, sh);
-            // new splits (FP32) and the loads they give
-            double vt[1] = {0.0};
+            block_sum<1, 2, 1>(gp, f2, k1, shf, shi);
+            const float T = f2[0], W = f2[1];
+            const float slack = 4e-6f * (T + W) + 1e-30f;
+            const StarEdges<WEIGHTED, R> E{ra, rs, rw, rha, cw, Bbuf, pr, p1, bbuf_p0, B};
+            float dl = star_root(E, -T - slack, W - T + slack, 0.0f, gp[0].x + gp[0].y, k1[0], shf, shi);
+            // far from the current hub load, FP32 levels in lh's frame are too coarse: recentre
+            // at lh + dl (the leaf levels are then small differences) and solve again
+            if (fabsf(dl) > ldexpf(fabsf(lh.x), -12)) {
+                float2 F = lh;
+                pair_add(F, dl, 0.0f);
+                gp[0] = make_float2(0.0f, 0.0f);
+                k1[0] = 0;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int32_t p = p0 + (int32_t)threadIdx.x + r * B;
-                if (p < p1) {
+                for (int r = 0; r < R; ++r) {
+                    if (rl[r] >= 0) {
+                        const float t = hub_share((rha >> r) & 1u, rs[r], rw[r]);
+                        ra[r] = frame_level(star_load<PACKED>(io, rl[r]), F, t);
+                        float hh, ll;
+                        two_sum(share(ra[r], rw[r], 0.0f), -t, hh, ll);
+                        pair_acc(gp[0].x, gp[0].y, hh, ll);
+                        k1[0] += piece(ra[r], rw[r], 0.0f) == 1;
+                    }
+                }
+                for (int32_t p = pr + (int32_t)threadIdx.x; p < p1; p += B) {
                     int32_t a, b;
                     star_ends<PACKED>(io, p, a, b);
                     const bool ha = a == h;
-                    const float wf = WEIGHTED ? __ldg(cw + p) : 1.0f;
-                    const double w = rw[r];
-                    const double t = share(rB[r], w, lam);
-                    const float snew = fminf(fmaxf(ha ? (float)t : (float)(w - t), 0.0f), wf);
-                    const double ta = ha ? (double)snew : w - (double)snew;
-                    __stcg(cs + p, snew);
-                    star_store<PACKED>(io, ha ? b : a, rB[r] + w - ta);
-                    vt[0] += ta;
+                    const float w = WEIGHTED ? __ldg(cw + p) : 1.0f;
+                    const float t = Bbuf[p - bbuf_p0].y;
+                    const float av = frame_level(star_load<PACKED>(io, ha ? b : a), F, t);
+                    Bbuf[p - bbuf_p0] = make_float2(av, t);
+                    float hh, ll;
+                    two_sum(share(av, w, 0.0f), -t, hh, ll);
+                    pair_acc(gp[0].x, gp[0].y, hh, ll);
+                    k1[0] += piece(av, w, 0.0f) == 1;
+                }
+                float fz[2] = {0.0f, 0.0f};
+                block_sum<1, 2, 1>(gp, fz, k1, shf, shi);
+                const float g0 = ((gp[0].x - dl) + gp[0].y);
+                const float sl2 = slack + 4e-6f * fabsf(dl);
+                dl = star_root(E, -T - dl - sl2, W - T - dl + sl2, dl, g0, k1[0], shf, shi);
+            }
+            // new splits and the load changes they make
+            float hub_hi = 0.0f, hub_lo = 0.0f;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (rl[r] >= 0) {
+                    const int32_t p = p0 + (int32_t)threadIdx.x + r * B;
+                    const bool ha = (rha >> r) & 1u;
+                    const float t = share(ra[r], rw[r], dl);
+                    const float s_new = fminf(fmaxf(ha ? t : rw[r] - t, 0.0f), rw[r]);
+                    star_apply<PACKED>(io, cs, p, ha, rl[r], rs[r], s_new, hub_hi, hub_lo);
                 }
             }
             for (int32_t p = pr + (int32_t)threadIdx.x; p < p1; p += B) {
                 int32_t a, b;
                 star_ends<PACKED>(io, p, a, b);
                 const bool ha = a == h;
-                const float wf = WEIGHTED ? __ldg(cw + p) : 1.0f;
-                const double w = (double)wf;
-                const double Bj = Bbuf[p - bbuf_p0];
-                const double t = share(Bj, w, lam);
-                const float snew = fminf(fmaxf(ha ? (float)t : (float)(w - t), 0.0f), wf);
-                const double ta = ha ? (double)snew : w - (double)snew;
-                __stcg(cs + p, snew);
-                star_store<PACKED>(io, ha ? b : a, Bj + w - ta);
-                vt[0] += ta;
+                const float w = WEIGHTED ? __ldg(cw + p) : 1.0f;
+                const float sv = __ldcg(cs + p);
+                const float t = share(Bbuf[p - bbuf_p0].x, w, dl);
+                const float s_new = fminf(fmaxf(ha ? t : w - t, 0.0f), w);
+                star_apply<PACKED>(io, cs, p, ha, ha ? b : a, sv, s_new, hub_hi, hub_lo);
             }
-            block_sum<1>(vt, sh);
-            if (threadIdx.x == 0) star_store<PACKED>(io, h, Bh + vt[0]);
+            float2 dh[1] = {make_float2(hub_hi, hub_lo)};
+            float fz[1] = {0.0f};
+            int kz[1] = {0};
+            block_sum<1, 1, 1>(dh, fz, kz, shf, shi);
+            if (threadIdx.x == 0) {
+                float2 H = lh;
+                pair_add(H, dh[0].x, dh[0].y);
+                star_store<PACKED>(io, h, H);
+            }
         }
         if (k + 1 < S && !grid_barrier(bar, bar + 1, gridDim.x, err)) return;
     }
@@ -597,7 +714,7 @@ cudaError_t lowd_star_pass(lowd_ctx* h) {
     const int32_t* shb = h->star_seg_hub;
     const float* pcw = h->cw;
     float* pcs = h->cs;
-    double* pbb = h->star_bbuf;
+    float2* pbb = h->star_bbuf;
     int32_t bp0 = (int32_t)h->star_p0;
     unsigned* bar = reinterpret_cast<unsigned*>(h->d_i32 + 12);
     int32_t* errp = h->d_i32 + 8;
