@@ -54,8 +54,17 @@ def _peaks():
 
 
 def _sweep_hash():
-    with open(os.path.join(ROOT, "paper_2307_15969_gb300", "csrc", "sweep.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the staged sweep kernel's source: its layout, the kernel and its launcher."""
+    with open(os.path.join(ROOT, "paper_2307_15969_gb300", "csrc", "sweep.cu")) as f:
+        s = f.read()
+    parts = []
+    for a, b in (("struct TmaLayout {", "// The same staging as k_sweep_tma"),
+                 ("cudaError_t launch_sweep_tma(", "cudaError_t launch_sweep_flow(")):
+        i, j = s.find(a), s.find(b)
+        if i < 0 or j < i:
+            return "missing"
+        parts.append(s[i:j])
+    return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
 
 
 def _traffic_per_pass():
@@ -325,6 +334,24 @@ def leg_unpruned(torch, pkg, stream, g, du, dv, dw, T, peak, peak_kind):
                         "peak_kind": peak_kind, "bytes_per_update": bpu,
                         "chain": "Delta = classes per pass; a pass is at least one class-to-class "
                                  "dependency step per class"}}
+    pkg.lowd_free(h)
+    # the same graph with hub-star block updates (automatic threshold): fewer dependent steps
+    # per pass (plain classes + star steps), each pass also a larger descent of sum l^2
+    h = pkg.lowd_load_graph(g.n, du, dv, dw, stream=stream)
+    a.record(stream)
+    pkg.lowd_iterate(h, 0, schedule=2, hub_stars=1)
+    b.record(stream)
+    b.synchronize()
+    prep_s = a.elapsed_time(b)
+    sec_s = sweep_launch_seconds(torch, pkg, stream, h, T)
+    st2 = pkg.lowd_iterate(h, 0)
+    info = pkg.lowd_get_info(h)
+    out["hub_stars"] = {"star_threshold": info["star_threshold"], "star_steps": info["star_steps"],
+                        "stars": info["stars"], "star_edges": info["star_edges"],
+                        "plain_classes": info["classes"] - info["star_steps"],
+                        "dependent_steps_per_pass": info["classes"], "pass_ms": sec_s / T * 1e3,
+                        "prepare_ms": prep_s, "sum_load_sq_after": st2["sum_load_sq"],
+                        "passes_timed": T}
     pkg.lowd_free(h)
     del flush
     return out
