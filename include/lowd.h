@@ -94,9 +94,12 @@ typedef struct {
                              minimiser of the sum of squared loads over them, all else fixed
                              (Sec. III-C's local optimality over a block of edges; a one-leaf
                              star is Algorithm 1's update), so sum l^2 still never rises and
-                             the loads converge to the same optimum.  The automatic threshold
-                             is the smallest power of two 2^k (k >= 1) with at most 2^(k-1)
-                             nodes of degree >= 2^k.  lowd_get_edge_order then lists the plain
+                             the loads converge to the same optimum.  The automatic threshold:
+                             schedule 1, the smallest power of two >= half the maximum degree
+                             (the near-universal nodes: the fewest steps for the stars' faster
+                             descent); schedule 2, the smallest power of two 2^k (k >= 1) with
+                             at most 2^(k-1) nodes of degree >= 2^k (also takes the hubs' edges
+                             out of the level order).  lowd_get_edge_order then lists the plain
                              classes, then one block per star step; lowd_info reports the
                              threshold, steps, stars and star edges */
 } lowd_options;

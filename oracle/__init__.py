@@ -474,11 +474,18 @@ def solve(n, u, v, w=None, T: int = 100, prune_first: bool = True, order=None):
                 rho=(Wb / scale / S.shape[0]) if S.shape[0] else 0.0)
 
 
-def auto_hub_threshold(n, u, v):
-    """The automatic hub threshold of the hub-star pass: the smallest power of two 2^k
-    (k >= 1) such that at most 2^(k-1) nodes have (unweighted) degree >= 2^k (so at most
-    half as many hubs as the threshold).  Returns an int (2^30 if no k up to 30 qualifies)."""
+def auto_hub_threshold(n, u, v, schedule: int = 2):
+    """The automatic hub threshold of the hub-star pass.  Schedule 1: the smallest power of two
+    p >= 2 with 2p >= the maximum (unweighted) degree.  Schedule 2: the smallest power of two
+    2^k (k >= 1) such that at most 2^(k-1) nodes have degree >= 2^k (so at most half as many
+    hubs as the threshold).  Returns an int (2^30 if no k up to 30 qualifies)."""
     deg = np.bincount(np.asarray(u, np.int64), minlength=n) + np.bincount(np.asarray(v, np.int64), minlength=n)
+    if schedule == 1:
+        dmax = int(deg.max()) if deg.shape[0] else 0
+        p = 2
+        while 2 * p < dmax and p < (1 << 30):
+            p *= 2
+        return p
     for k in range(1, 31):
         if int((deg >= (1 << k)).sum()) <= (1 << (k - 1)):
             return 1 << k

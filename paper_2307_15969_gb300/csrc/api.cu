@@ -1,6 +1,7 @@
 // C ABI entry points (include/lowd.h): argument checks, host/device marshalling, call
 // order, and dispatch to the graph, sweep and extraction units.
 #include <atomic>
+#include <mutex>
 #include <new>
 
 #include "ctx.cuh"
@@ -27,6 +28,38 @@ int lowd_device_sms() {
     return v;
 }
 
+// The library's memory pool on the current device, created on first use.  Up to
+// kPoolKeepBytes of freed memory stay reserved in it between calls; beyond that, freed memory
+// goes back to the device at the next synchronisation.
+cudaMemPool_t lowd_pool() {
+    constexpr int kMaxDev = 64;
+    constexpr uint64_t kPoolKeepBytes = 8ull << 30;
+    static cudaMemPool_t pools[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = kPoolKeepBytes;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
 namespace {
 
 lowd_status check_handle(lowd_handle h) { return h ? LOWD_OK : LOWD_ERR_INVALID_ARG; }
@@ -42,15 +75,17 @@ lowd_status to_caller(lowd_ctx* h, T* dst, const T* src_dev, size_t n) {
 }
 
 void free_all(lowd_ctx* h) {
-    dfree(&h->u); dfree(&h->v); dfree(&h->w); dfree(&h->wu); dfree(&h->map);
-    dfree(&h->sort_perm); dfree(&h->removal_round);
-    dfree(&h->perm); dfree(&h->coff); dfree(&h->coff_real); dfree(&h->cuv); dfree(&h->crk);
-    dfree(&h->cw); dfree(&h->cs); dfree(&h->l); dfree(&h->l_lo);
-    dfree(&h->s2_ctab); dfree(&h->s2_beg); dfree(&h->s2_ea); dfree(&h->s2_eb);
-    dfree(&h->s2_srcA); dfree(&h->s2_srcB); dfree(&h->s2_lp); dfree(&h->s2_blob); dfree(&h->s2_blobo);
-    dfree(&h->star_step_seg); dfree(&h->star_seg_beg); dfree(&h->star_seg_hub); dfree(&h->star_bbuf);
-    dfree(&h->tmp); h->tmp_cap = 0;
-    dfree(&h->d_stats); dfree(&h->d_i64); dfree(&h->d_i32);
+    dfree(h, &h->u); dfree(h, &h->v); dfree(h, &h->w); dfree(h, &h->wu); dfree(h, &h->map);
+    dfree(h, &h->sort_perm); dfree(h, &h->removal_round);
+    dfree(h, &h->perm); dfree(h, &h->coff); dfree(h, &h->coff_real); dfree(h, &h->cuv); dfree(h, &h->crk);
+    dfree(h, &h->cw); dfree(h, &h->cs); dfree(h, &h->l); dfree(h, &h->l_lo);
+    dfree(h, &h->s2_ctab); dfree(h, &h->s2_beg); dfree(h, &h->s2_ea); dfree(h, &h->s2_eb);
+    dfree(h, &h->s2_srcA); dfree(h, &h->s2_srcB); dfree(h, &h->s2_lp); dfree(h, &h->s2_blob); dfree(h, &h->s2_blobo);
+    dfree(h, &h->star_step_seg); dfree(h, &h->star_seg_beg); dfree(h, &h->star_seg_hub); dfree(h, &h->star_bbuf);
+    if (h->tmp) cudaFree(h->tmp);   // the sort scratch is a plain allocation (need_tmp)
+    h->tmp = nullptr;
+    h->tmp_cap = 0;
+    dfree(h, &h->d_stats); dfree(h, &h->d_i64); dfree(h, &h->d_i32);
     if (h->h_pin) cudaFreeHost(h->h_pin);
     h->h_pin = nullptr;
     free(h->coff_h);
@@ -117,7 +152,7 @@ lowd_status current_loads(lowd_ctx* h, float** out) {
     LOWD_LAUNCH(k_to_float, grid_for(h->n), 256, 0, h->st, L64, h->n, *out);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-    dfree(&L64);
+    dfree(h, &L64);
     if (e != cudaSuccess) return h->fail(e);
     return LOWD_OK;
 }
@@ -166,7 +201,7 @@ lowd_status lowd_load_graph(int32_t n, int64_t m, const int32_t* u, const int32_
     lowd_status s = LOWD_OK;
     if (mem == LOWD_MEM_HOST && m > 0) {
         if ((s = dalloc(h, &cu, m)) || (s = dalloc(h, &cv, m)) || (w && (s = dalloc(h, &cw, m)))) {
-            dfree(&cu); dfree(&cv); dfree(&cw);
+            dfree(h, &cu); dfree(h, &cv); dfree(h, &cw);
             free_all(h); delete h;
             return s;
         }
@@ -182,7 +217,7 @@ lowd_status lowd_load_graph(int32_t n, int64_t m, const int32_t* u, const int32_
     } else {
         cudaStreamSynchronize(h->st);
     }
-    dfree(&cu); dfree(&cv); dfree(&cw);
+    dfree(h, &cu); dfree(h, &cv); dfree(h, &cw);
     if (s != LOWD_OK) {
         free_all(h);
         delete h;
@@ -243,7 +278,7 @@ lowd_status lowd_extract(lowd_handle h, int32_t* S, int32_t* S_size, double* rho
             LOWD_LAUNCH(k_scatter_loads, grid_for(h->n), 256, 0, h->st, l, h->n, h->map, full);
             if (h->mem != LOWD_MEM_DEVICE) {
                 s = to_caller(h, loads, full, (size_t)h->n0);
-                dfree(&full);
+                dfree(h, &full);
                 if (s) break;
             }
         }
@@ -253,8 +288,8 @@ lowd_status lowd_extract(lowd_handle h, int32_t* S, int32_t* S_size, double* rho
             if (e != cudaSuccess) { s = h->fail(e); break; }
         }
     } while (0);
-    if (h->mem != LOWD_MEM_DEVICE) dfree(&Sdev);
-    dfree(&l);
+    if (h->mem != LOWD_MEM_DEVICE) dfree(h, &Sdev);
+    dfree(h, &l);
     return s;
 }
 
@@ -299,7 +334,7 @@ lowd_status lowd_get_ldd(lowd_handle h, double rel_tol, int32_t* shell, double* 
         if (e != cudaSuccess) { s = h->fail(e); break; }
         *n_shells = ns;
     } while (0);
-    dfree(&l); dfree(&sh); dfree(&se); dfree(&lam);
+    dfree(h, &l); dfree(h, &sh); dfree(h, &se); dfree(h, &lam);
     return s;
 }
 
@@ -344,7 +379,7 @@ lowd_status lowd_get_graph(lowd_handle h, int32_t* u, int32_t* v, float* w) {
             if (cudaGetLastError() != cudaSuccess) r = h->fail(cudaGetLastError());
             if (r == LOWD_OK) r = to_caller(h, w, ones, (size_t)h->m);
             cudaStreamSynchronize(h->st);
-            dfree(&ones);
+            dfree(h, &ones);
             LOWD_TRY(r);
         }
     }
@@ -365,7 +400,7 @@ lowd_status lowd_get_splits(lowd_handle h, float* s) {
         cudaError_t e = cudaStreamSynchronize(h->st);
         if (e != cudaSuccess) r = h->fail(e);
     }
-    dfree(&d);
+    dfree(h, &d);
     return r;
 }
 
@@ -381,7 +416,7 @@ lowd_status lowd_apply_splits_dev(lowd_ctx* h, const float* d) {
     if (h->m > 0) LOWD_LAUNCH(k_clamp_splits, grid_for(h->m), 256, 0, h->st, d, h->w, h->m, c);
     lowd_status r = lowd_sweep_load_canonical(h, c);
     cudaStreamSynchronize(h->st);
-    dfree(&c);
+    dfree(h, &c);
     if (r) return r;
     double st3[3];
     return lowd_sweep_rederive(h, st3);
@@ -400,7 +435,7 @@ lowd_status lowd_set_splits(lowd_handle h, const float* s) {
         r = h->fail(cudaGetLastError());
     if (r == LOWD_OK) r = lowd_apply_splits_dev(h, d);
     cudaStreamSynchronize(h->st);
-    dfree(&d);
+    dfree(h, &d);
     return r;
 }
 
@@ -414,7 +449,7 @@ lowd_status lowd_get_loads(lowd_handle h, float* loads) {
         cudaError_t e = cudaStreamSynchronize(h->st);
         if (e != cudaSuccess) r = h->fail(e);
     }
-    dfree(&l);
+    dfree(h, &l);
     return r;
 }
 
@@ -435,7 +470,7 @@ lowd_status lowd_get_edge_order(lowd_handle h, int32_t* perm, int32_t* class_off
         lowd_status r = lowd_sweep_edge_order(h, d);
         if (r == LOWD_OK) r = to_caller(h, perm, d, (size_t)h->m);
         cudaStreamSynchronize(h->st);
-        dfree(&d);
+        dfree(h, &d);
         LOWD_TRY(r);
     }
     LOWD_TRY(to_caller(h, class_offsets, h->coff_real, (size_t)h->C + h->star_S + 1));

@@ -133,18 +133,26 @@ struct lowd_ctx {
         if (s_ != LOWD_OK) return s_;         \
     } while (0)
 
+// Device buffers of a handle come from the library's stream-ordered memory pool (one per
+// device): allocated and freed in the handle's stream order, so a call's temporaries cost no
+// device-wide synchronisation, and freed memory stays reserved in the pool for the next call
+// (up to lowd_pool's threshold) instead of being unmapped and mapped again.
+cudaMemPool_t lowd_pool();
+
 template <class T>
 inline lowd_status dalloc(lowd_ctx* h, T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+    cudaMemPool_t pool = lowd_pool();
+    if (!pool) return h->fail(cudaErrorMemoryAllocation);
+    cudaError_t e = cudaMallocFromPoolAsync((void**)p, sizeof(T) * count, pool, h->st);
     if (e != cudaSuccess) { *p = nullptr; return h->fail(e); }
     return LOWD_OK;
 }
 
 template <class T>
-inline void dfree(T** p) {
-    if (*p) cudaFree(*p);
+inline void dfree(lowd_ctx* h, T** p) {
+    if (*p) cudaFreeAsync(*p, h->st);
     *p = nullptr;
 }
 
@@ -174,9 +182,9 @@ struct StarSplit {
     int32_t* sid = nullptr;       // [ms] star edge ids
     int32_t* gu = nullptr;        // [m_plain] ends of the plain edges
     int32_t* gv = nullptr;
-    void release();
+    void release(lowd_ctx* h);
 };
-lowd_status lowd_star_split(lowd_ctx* h, int32_t hub_tau, StarSplit* sp);
+lowd_status lowd_star_split(lowd_ctx* h, int32_t hub_tau, int schedule, StarSplit* sp);
 lowd_status lowd_star_blocks(lowd_ctx* h, const StarSplit& sp, int64_t p0, int32_t C_plain, int64_t m_real_plain);
 cudaError_t lowd_star_pass(lowd_ctx* h);
 

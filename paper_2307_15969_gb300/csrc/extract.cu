@@ -133,8 +133,8 @@ lowd_status lowd_extract_best(lowd_ctx* h, const float* loads_dev, int32_t* S_de
     Best* part = nullptr;
     lowd_status s = LOWD_OK;
     auto cleanup = [&]() {
-        dfree(&key[0]); dfree(&key[1]); dfree(&val[0]); dfree(&val[1]); dfree(&pos);
-        dfree(&flag); dfree(&fpos); dfree(&bucket); dfree(&excl); dfree(&part);
+        dfree(h, &key[0]); dfree(h, &key[1]); dfree(h, &val[0]); dfree(h, &val[1]); dfree(h, &pos);
+        dfree(h, &flag); dfree(h, &fpos); dfree(h, &bucket); dfree(h, &excl); dfree(h, &part);
     };
     do {
         if ((s = h->need_tmp(lowd_sort_tmp_bytes(m > n ? m : n)))) break;
@@ -398,8 +398,8 @@ lowd_status lowd_ldd_export(lowd_ctx* h, const float* loads_dev, double rel_tol,
     int64_t* excl = nullptr;
     lowd_status s = LOWD_OK;
     auto cleanup = [&]() {
-        dfree(&key[0]); dfree(&key[1]); dfree(&val[0]); dfree(&val[1]); dfree(&pos);
-        dfree(&cut); dfree(&cpos); dfree(&bucket); dfree(&excl);
+        dfree(h, &key[0]); dfree(h, &key[1]); dfree(h, &val[0]); dfree(h, &val[1]); dfree(h, &pos);
+        dfree(h, &cut); dfree(h, &cpos); dfree(h, &bucket); dfree(h, &excl);
     };
     do {
         if ((s = h->need_tmp(lowd_sort_tmp_bytes(m > n ? m : n)))) break;

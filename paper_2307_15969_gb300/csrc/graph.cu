@@ -321,8 +321,8 @@ lowd_status lowd_graph_load(lowd_ctx* h, const int32_t* du, const int32_t* dv, c
     int32_t* pos = nullptr;
     lowd_status s = LOWD_OK;
     auto cleanup = [&]() {
-        dfree(&keys[0]); dfree(&keys[1]); dfree(&idx[0]); dfree(&idx[1]);
-        dfree(&first); dfree(&pos);
+        dfree(h, &keys[0]); dfree(h, &keys[1]); dfree(h, &idx[0]); dfree(h, &idx[1]);
+        dfree(h, &first); dfree(h, &pos);
     };
     do {
         if ((s = dalloc(h, &h->d_i32, 16))) break;
@@ -403,7 +403,7 @@ lowd_status lowd_graph_max_degree(lowd_ctx* h) {
     int32_t md = 0;
     cudaError_t e = cudaMemcpyAsync(&md, h->d_i32 + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    dfree(&cnt);
+    dfree(h, &cnt);
     if (e != cudaSuccess) return h->fail(e);
     h->max_deg = md;
     return LOWD_OK;
@@ -427,10 +427,10 @@ lowd_status lowd_graph_prune(lowd_ctx* h, int32_t* rounds_out) {
     int64_t* nwu = nullptr;
     lowd_status s = LOWD_OK;
     auto cleanup = [&]() {
-        dfree(&deg); dfree(&dkey[0]); dfree(&dkey[1]); dfree(&dval[0]); dfree(&dval[1]);
-        dfree(&act); dfree(&act2); dfree(&keep); dfree(&pos);
-        dfree(&eu[0]); dfree(&eu[1]); dfree(&ev[0]); dfree(&ev[1]); dfree(&ew[0]); dfree(&ew[1]);
-        dfree(&keepe); dfree(&epos); dfree(&nmap); dfree(&nu); dfree(&nv); dfree(&nw); dfree(&nwu);
+        dfree(h, &deg); dfree(h, &dkey[0]); dfree(h, &dkey[1]); dfree(h, &dval[0]); dfree(h, &dval[1]);
+        dfree(h, &act); dfree(h, &act2); dfree(h, &keep); dfree(h, &pos);
+        dfree(h, &eu[0]); dfree(h, &eu[1]); dfree(h, &ev[0]); dfree(h, &ev[1]); dfree(h, &ew[0]); dfree(h, &ew[1]);
+        dfree(h, &keepe); dfree(h, &epos); dfree(h, &nmap); dfree(h, &nu); dfree(h, &nv); dfree(h, &nw); dfree(h, &nwu);
     };
     do {
         if ((s = dalloc(h, &deg, n))) break;
@@ -544,7 +544,7 @@ lowd_status lowd_graph_prune(lowd_ctx* h, int32_t* rounds_out) {
             LOWD_LAUNCH(k_emit_edges, grid_for(m), kT, 0, st, h->u, h->v, h->w, h->wu, m, keepe, epos, pos, nu, nv, nw, nwu);
         if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
         // swap in H
-        dfree(&h->u); dfree(&h->v); dfree(&h->w); dfree(&h->wu); dfree(&h->map);
+        dfree(h, &h->u); dfree(h, &h->v); dfree(h, &h->w); dfree(h, &h->wu); dfree(h, &h->map);
         h->u = nu; h->v = nv; h->w = nw; h->wu = nwu; h->map = nmap;
         nu = nv = nullptr; nw = nullptr; nwu = nullptr; nmap = nullptr;
         h->n = (int32_t)N;

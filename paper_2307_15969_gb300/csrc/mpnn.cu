@@ -425,49 +425,130 @@ __global__ void k_mp_dA(int64_t cnt, const float* __restrict__ G, const bf16* __
     }
 }
 
-// Per-block partials of dW = X^T dA (X = [h, m], 128 inputs) and db = sum dA.  Thread t owns
-// output column j = t % 64 for inputs i = 32 (t / 64) .. +31; nodes staged 32 at a time.
-constexpr int kDWNodes = 32;
-constexpr int kDWCols = 128 * 64 + 64;
-__global__ void __launch_bounds__(256) k_mp_dW(int32_t n, const bf16* __restrict__ h, const bf16* __restrict__ mm,
-                                               const float* __restrict__ dA, float* __restrict__ part) {
-    __shared__ float sX[kDWNodes][128];
-    __shared__ float sD[kDWNodes][64];
-    const int t = threadIdx.x;
-    const int j = t & 63, ig = t >> 6;
-    float acc[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) acc[k] = 0.0f;
-    float accb = 0.0f;
-    const int64_t chunks = ((int64_t)n + kDWNodes - 1) / kDWNodes;
-    for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
-        const int64_t v0 = ch * kDWNodes;
-        __syncthreads();
-        for (int i = t; i < kDWNodes * 128; i += 256) {
-            const int r = i >> 7, c = i & 127;
-            const int64_t v = v0 + r;
-            float x = 0.0f;
-            if (v < n) x = __bfloat162float(c < 64 ? h[v * 64 + c] : mm[v * 64 + c - 64]);
-            sX[r][c] = x;
+constexpr int kDWCols = 128 * 64 + 64;   // per-block partials: [in][out] weights, then the bias
+
+// Weight gradient of a 128 -> 64 layer on the tensor cores: per CTA, D[128 x 64] = X^T dA
+// over its chunks of 64 nodes (X = [h, m] bf16, the product's K = nodes), with dA the bf16
+// copy that the backward-data product also uses; FP32 accumulators in tensor memory.  Each
+// chunk is staged transposed (rows = X's columns / dA's columns, K-major) into one of two
+// shared-memory buffers while the other buffer's four MMAs run; the commit of a buffer is
+// awaited (bounded) before the buffer is staged again.  The bias gradient (sum of the FP32
+// dA over nodes) is summed on the CUDA cores while staging.  Epilogue: warp w reads tensor
+// lanes 32w.. (rows of X^T) and writes the CTA's partials in the layout k_mp_dW_final reduces.
+constexpr int kDwChunk = 64;                                  // nodes per staged chunk
+constexpr uint32_t kDwABytes = 128u * kDwChunk * 2u;          // X^T tile
+constexpr uint32_t kDwBBytes = 64u * kDwChunk * 2u;           // dA^T tile
+constexpr int kDwSmem = 56 * 1024;                            // >= 2 (A + B); caps residency at 4 CTAs
+__global__ void __launch_bounds__(128) k_umma_dW(int32_t n, const bf16* __restrict__ h, const bf16* __restrict__ mm,
+                                                 const bf16* __restrict__ dAb, const float* __restrict__ dA,
+                                                 float* __restrict__ part, int32_t* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t s_taddr;
+    __shared__ int32_t s_ok;
+    __shared__ float s_bias[64];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        tmem_alloc(&s_taddr, 64u);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        s_ok = 1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = s_taddr;
+    constexpr uint32_t idesc = umma_idesc_bf16(128, 64);
+    const int64_t chunks = ((int64_t)n + kDwChunk - 1) / kDwChunk;
+    float bsum = 0.0f;   // column tid & 63 of the bias gradient, nodes of this thread's half
+    int32_t it = 0;
+    bool failed = false;
+    for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x, ++it) {
+        const int b = it & 1;
+        unsigned char* sA = smem + (uint32_t)b * (kDwABytes + kDwBBytes);
+        unsigned char* sB = sA + kDwABytes;
+        if (it >= 2) {   // the MMAs that last read this buffer (two chunks ago) must be done
+            if (tid == 0) {
+                const uint32_t par = (uint32_t)(((it - 2) >> 1) & 1);
+                uint32_t spins = 0;
+                bool ok = mbar_try_wait(&bar[b], par);
+                while (!ok && ++spins < kUmmaWaitLimit) ok = mbar_try_wait(&bar[b], par);
+                s_ok = ok ? 1 : 0;
+            }
+            __syncthreads();
+            if (!s_ok) { failed = true; break; }
         }
-        for (int i = t; i < kDWNodes * 64; i += 256) {
-            const int r = i >> 6, c = i & 63;
-            const int64_t v = v0 + r;
-            sD[r][c] = v < n ? dA[v * 64 + c] : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int r = 0; r < kDWNodes; ++r) {
-            const float d = sD[r][j];
-            if (ig == 0) accb += d;
+        const int64_t v0 = ch * kDwChunk;
+        // X^T: row f (feature 0..127), K = node; 16-byte global loads of 8 features
+        for (int idx = tid; idx < kDwChunk * 16; idx += 128) {
+            const int node = idx & (kDwChunk - 1), fc = idx >> 6;
+            const int64_t v = v0 + node;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (v < n) val = *reinterpret_cast<const uint4*>((fc < 8 ? h + v * 64 + fc * 8 : mm + v * 64 + (fc - 8) * 8));
+            const uint16_t* e8 = reinterpret_cast<const uint16_t*>(&val);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) acc[k] += sX[r][ig * 32 + k] * d;
+            for (int e = 0; e < 8; ++e)
+                *reinterpret_cast<uint16_t*>(sA + umma_tile_offset(fc * 8 + e, node, kDwChunk)) = e8[e];
+        }
+        // dA^T: row j (output column 0..63), K = node; the bias gradient from the FP32 dA
+        for (int idx = tid; idx < kDwChunk * 64; idx += 128) {
+            const int node = idx >> 6, j = idx & 63;
+            const int64_t v = v0 + node;
+            uint16_t bits = 0;
+            if (v < n) {
+                bits = *reinterpret_cast<const uint16_t*>(dAb + v * 64 + j);
+                bsum += dA[v * 64 + j];
+            }
+            *reinterpret_cast<uint16_t*>(sB + umma_tile_offset(j, node, kDwChunk)) = bits;
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+            for (int ks = 0; ks < kDwChunk / 16; ++ks)
+                umma_bf16(taddr, umma_desc(a0 + ks * 256, 128, kDwChunk * 16), umma_desc(b0 + ks * 256, 128, kDwChunk * 16),
+                          idesc, (it > 0 || ks > 0) ? 1u : 0u);
+            umma_commit(&bar[b]);
         }
     }
+    // wait for the last chunk's MMAs (a commit covers every earlier MMA of the thread)
+    if (it > 0 && tid == 0) {
+        const int last = it - 1;
+        const uint32_t par = (uint32_t)((last >> 1) & 1);
+        uint32_t spins = 0;
+        bool ok = mbar_try_wait(&bar[last & 1], par);
+        while (!ok && ++spins < kUmmaWaitLimit) ok = mbar_try_wait(&bar[last & 1], par);
+        if (!ok) failed = true;
+        s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_ok) failed = true;
+    tc_fence_after();
     float* out = part + (size_t)blockIdx.x * kDWCols;
+    const int r = warp * 32 + lane;   // row of X^T = input feature
+    if (!failed) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float vv[16];
+            if (it > 0) tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, vv);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) out[(ig * 32 + k) * 64 + j] = acc[k];
-    if (ig == 0) out[128 * 64 + j] = accb;
+            for (int i = 0; i < 16; ++i) out[r * 64 + c0 + i] = it > 0 ? vv[i] : 0.0f;
+        }
+    } else if (tid == 0) {
+        atomicOr(err, 2);
+    }
+    if (tid >= 64) s_bias[tid - 64] = bsum;
+    __syncthreads();
+    if (tid < 64) out[128 * 64 + tid] = bsum + s_bias[tid];
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, 64u);
 }
 
 // reduce the dW partials: grad W_l [out][in] and grad b_l
@@ -800,13 +881,13 @@ lowd_status mp_backward(lowd_mpnn_ctx* c) {
     LOWD_LAUNCH(k_mp_reduce_cols, 1, 64, 0, c->st, c->part, (int)gh, 64, c->g + kOffQ);
     float* G = c->G;
     float* Gn = c->G2;
-    const unsigned gd = blocks_for(((int64_t)n + kDWNodes - 1) / kDWNodes, 1) > (unsigned)kPartBlocks
-                            ? (unsigned)kPartBlocks
-                            : blocks_for(((int64_t)n + kDWNodes - 1) / kDWNodes, 1);
+    const int64_t dw_chunks = ((int64_t)n + kDwChunk - 1) / kDwChunk;
+    const unsigned gdw = dw_chunks > kPartBlocks ? (unsigned)kPartBlocks : (unsigned)dw_chunks;
+    MP_CK(cudaFuncSetAttribute(k_umma_dW, cudaFuncAttributeMaxDynamicSharedMemorySize, kDwSmem));
     for (int l = kL - 1; l >= 0; --l) {
         LOWD_LAUNCH(k_mp_dA, blocks_for((int64_t)n * kH, kT), kT, 0, c->st, (int64_t)n * kH, G, c->h[l + 1], c->dA, c->dAb);
-        LOWD_LAUNCH(k_mp_dW, gd, 256, 0, c->st, n, c->h[l], c->mm[l], c->dA, c->part);
-        LOWD_LAUNCH(k_mp_dW_final, blocks_for(kDWCols, kT), kT, 0, c->st, c->part, (int)gd, c->g + off_W(l), c->g + off_b(l));
+        LOWD_LAUNCH(k_umma_dW, gdw, 128, kDwSmem, c->st, n, c->h[l], c->mm[l], c->dAb, c->dA, c->part, c->d_err);
+        LOWD_LAUNCH(k_mp_dW_final, blocks_for(kDWCols, kT), kT, 0, c->st, c->part, (int)gdw, c->g + off_W(l), c->g + off_b(l));
         MP_CK((launch_umma<64, 128, EPI_F32>(c, c->dAb, nullptr, c->wtb + (size_t)l * kH * 2 * kH, nullptr, nullptr,
                                               c->dX)));
         LOWD_LAUNCH(k_mp_prevG, gw, kT, 0, c->st, n, c->row, c->nbr, c->dX, Gn);
@@ -982,10 +1063,10 @@ lowd_status lowd_warm_start(lowd_handle h, lowd_mpnn c) {
     LOWD_TRY(dalloc(h, &d, h->m));
     if (h->m > 0) LOWD_LAUNCH(k_mp_splits, blocks_for(h->m, kT), kT, 0, c->st, h->m, c->sigma, c->weighted ? c->w : nullptr, d);
     e = cudaStreamSynchronize(c->st);
-    if (e != cudaSuccess) { dfree(&d); return h->fail(e); }
+    if (e != cudaSuccess) { dfree(h, &d); return h->fail(e); }
     s = lowd_apply_splits_dev(h, d);
     cudaStreamSynchronize(h->st);
-    dfree(&d);
+    dfree(h, &d);
     return s;
 }
 

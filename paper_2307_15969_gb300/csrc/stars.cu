@@ -17,8 +17,12 @@
 // hub form a star, and the stars of a step are vertex-disjoint (a leaf has one edge per
 // step, hubs are never leaves).  A pass runs Algorithm 1 over the plain edges (their own
 // schedule), then the steps in order, the stars of a step in parallel.  The automatic
-// threshold is the smallest power of two 2^k (k >= 1) with at most 2^(k-1) nodes of degree
-// >= 2^k.
+// threshold depends on the schedule.  Schedule 1 (circle colouring: n - 1 classes whatever
+// the stars take away) only needs the stars' faster descent, and the near-universal nodes
+// give it with the fewest steps: the smallest power of two >= half the maximum degree.
+// Schedule 2 (level order: at least the plain subgraph's maximum degree in classes) also
+// needs the hubs' edges out of the plain subgraph: the smallest power of two 2^k (k >= 1)
+// with at most 2^(k-1) nodes of degree >= 2^k.
 //
 // Execution.  One cooperative launch per pass runs every step; blocks take the stars of a
 // step, one star per block at a time, and meet at a bounded grid barrier between steps.  A
@@ -525,17 +529,18 @@ k_star_steps(int32_t S, const int32_t* __restrict__ step_seg, const int32_t* __r
 
 }  // namespace
 
-void StarSplit::release() {
-    dfree(&dfull);
-    dfree(&pid);
-    dfree(&sid);
-    dfree(&gu);
-    dfree(&gv);
+void StarSplit::release(lowd_ctx* h) {
+    dfree(h, &dfull);
+    dfree(h, &pid);
+    dfree(h, &sid);
+    dfree(h, &gu);
+    dfree(h, &gv);
 }
 
 // Classify the edges of the current graph for hub stars (hub_tau: 1 automatic, >= 2 the
-// threshold).  With no star edge the split is released and reports all edges plain.
-lowd_status lowd_star_split(lowd_ctx* h, int32_t hub_tau, StarSplit* sp) {
+// threshold) for the given schedule.  With no star edge the split is released and reports all
+// edges plain.
+lowd_status lowd_star_split(lowd_ctx* h, int32_t hub_tau, int schedule, StarSplit* sp) {
     cudaStream_t st = h->st;
     const int64_t m = h->m;
     const int32_t n = h->n;
@@ -551,7 +556,11 @@ lowd_status lowd_star_split(lowd_ctx* h, int32_t hub_tau, StarSplit* sp) {
         cudaMemsetAsync(sp->dfull, 0, sizeof(int32_t) * (size_t)n, st);
         LOWD_LAUNCH(k_star_degrees, grid_for(m), kT, 0, st, h->u, h->v, m, sp->dfull);
         int32_t tau = hub_tau;
-        if (tau == 1) {
+        if (tau == 1 && schedule == 1) {   // the near-universal nodes: degree >= ~max degree / 2
+            int64_t p = 2;
+            while (2 * p < (int64_t)h->max_deg && p < (1 << 30)) p *= 2;
+            tau = (int32_t)p;
+        } else if (tau == 1) {
             if ((s = dalloc(h, &cnt, 32))) break;
             cudaMemsetAsync(cnt, 0, 32 * sizeof(unsigned long long), st);
             LOWD_LAUNCH(k_degree_powers, grid_for(n), kT, 0, st, sp->dfull, n, cnt);
@@ -576,7 +585,7 @@ lowd_status lowd_star_split(lowd_ctx* h, int32_t hub_tau, StarSplit* sp) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { s = h->fail(e); break; }
         if (cnts[1] == 0) {   // no star edge: every edge is plain
-            sp->release();
+            sp->release(h);
             sp->m_plain = m;
             break;
         }
@@ -594,9 +603,9 @@ lowd_status lowd_star_split(lowd_ctx* h, int32_t hub_tau, StarSplit* sp) {
                         sp->gv);
         if (cudaGetLastError() != cudaSuccess) s = h->fail(cudaGetLastError());
     } while (0);
-    for (int i = 0; i < 2; ++i) { dfree(&fl[i]); dfree(&fp[i]); }
-    dfree(&cnt);
-    if (s) sp->release();
+    for (int i = 0; i < 2; ++i) { dfree(h, &fl[i]); dfree(h, &fp[i]); }
+    dfree(h, &cnt);
+    if (s) sp->release(h);
     return s;
 }
 
@@ -669,7 +678,7 @@ lowd_status lowd_star_blocks(lowd_ctx* h, const StarSplit& sp, int64_t p0, int32
         cudaMemcpyAsync(cnew + C_plain + 1, tail.data(), sizeof(int32_t) * tail.size(), cudaMemcpyHostToDevice, st);
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { s = h->fail(e); break; }
-        dfree(&h->coff_real);
+        dfree(h, &h->coff_real);
         h->coff_real = cnew;
         cnew = nullptr;
         h->star_tau = sp.tau;
@@ -680,8 +689,8 @@ lowd_status lowd_star_blocks(lowd_ctx* h, const StarSplit& sp, int64_t p0, int32
         h->star_maxseg = maxseg;
         if (cudaGetLastError() != cudaSuccess) s = h->fail(cudaGetLastError());
     } while (0);
-    dfree(&sk0); dfree(&sk1); dfree(&so0); dfree(&so1); dfree(&head); dfree(&hpos); dfree(&q0); dfree(&q1);
-    dfree(&cnew);
+    dfree(h, &sk0); dfree(h, &sk1); dfree(h, &so0); dfree(h, &so1); dfree(h, &head); dfree(h, &hpos); dfree(h, &q0); dfree(h, &q1);
+    dfree(h, &cnew);
     return s;
 }
 

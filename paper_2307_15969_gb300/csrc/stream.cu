@@ -800,17 +800,17 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
     int32_t *rb = nullptr, *pb = nullptr;
     lowd_status s = LOWD_OK;
     auto cleanup = [&]() {
-        sp.release();
-        dfree(&deg); dfree(&k32[0]); dfree(&k32[1]); dfree(&k64[0]); dfree(&k64[1]); dfree(&val[0]);
-        dfree(&val[1]); dfree(&succ); dfree(&pend); dfree(&level); dfree(&fr[0]); dfree(&fr[1]); dfree(&ctl);
-        dfree(&has_pred); dfree(&okey[0]); dfree(&okey[1]); dfree(&oval[0]); dfree(&oval[1]);
-        dfree(&gfirst); dfree(&glast); dfree(&rb); dfree(&pb);
+        sp.release(h);
+        dfree(h, &deg); dfree(h, &k32[0]); dfree(h, &k32[1]); dfree(h, &k64[0]); dfree(h, &k64[1]); dfree(h, &val[0]);
+        dfree(h, &val[1]); dfree(h, &succ); dfree(h, &pend); dfree(h, &level); dfree(h, &fr[0]); dfree(h, &fr[1]); dfree(h, &ctl);
+        dfree(h, &has_pred); dfree(h, &okey[0]); dfree(h, &okey[1]); dfree(h, &oval[0]); dfree(h, &oval[1]);
+        dfree(h, &gfirst); dfree(h, &glast); dfree(h, &rb); dfree(h, &pb);
     };
     const bool weighted = h->w != nullptr;
     do {
         if ((s = h->need_tmp(lowd_sort_tmp_bytes(2 * (h->m > n ? h->m : n) + 2)))) break;
         // ---- 0. hub stars: classify the edges, keep the plain ones for the level order
-        if ((s = lowd_star_split(h, h->hub_tau, &sp))) break;
+        if ((s = lowd_star_split(h, h->hub_tau, 2, &sp))) break;
         const int32_t* pid = sp.pid;
         const int64_t ms = sp.ms;
         if (pid) {
@@ -850,16 +850,16 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
             int c3 = radix_sort_pairs<uint32_t, int32_t>(k32[0], spare, k32[1], rk2, 2 * m, nbits, h->tmp, st);
             uint32_t* nodes = c3 ? k32[1] : k32[0];
             int32_t* rks = c3 ? rk2 : spare;
-            if ((s = dalloc(h, &succ, 2 * m))) { dfree(&rk2); break; }
-            if ((s = dalloc(h, &has_pred, 2 * m))) { dfree(&rk2); break; }
+            if ((s = dalloc(h, &succ, 2 * m))) { dfree(h, &rk2); break; }
+            if ((s = dalloc(h, &has_pred, 2 * m))) { dfree(h, &rk2); break; }
             LOWD_LAUNCH(k_successors, grid_for(2 * m), kT, 0, st, nodes, rks, 2 * m, ord, cu, succ, has_pred);
-            dfree(&rk2);
+            dfree(h, &rk2);
             // ord must survive: copy it out of the ping-pong buffers
             int32_t* ord_keep = nullptr;
             if ((s = dalloc(h, &ord_keep, m))) break;
             cudaMemcpyAsync(ord_keep, ord, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToDevice, st);
             ord = ord_keep;
-            dfree(&val[0]); dfree(&val[1]);
+            dfree(h, &val[0]); dfree(h, &val[1]);
             val[0] = ord_keep;   // freed by cleanup
             if ((s = dalloc(h, &pend, m))) break;
             if ((s = dalloc(h, &level, m))) break;

@@ -1050,12 +1050,12 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
     StarSplit sp;   // hub stars: the circle colouring covers the plain edges
     lowd_status s = LOWD_OK;
     auto cleanup = [&]() {
-        sp.release();
-        dfree(&key[0]); dfree(&key[1]); dfree(&val[0]); dfree(&val[1]);
-        dfree(&head); dfree(&hpos); dfree(&pcnt);
+        sp.release(h);
+        dfree(h, &key[0]); dfree(h, &key[1]); dfree(h, &val[0]); dfree(h, &val[1]);
+        dfree(h, &head); dfree(h, &hpos); dfree(h, &pcnt);
     };
     do {
-        if ((s = lowd_star_split(h, h->hub_tau, &sp))) break;
+        if ((s = lowd_star_split(h, h->hub_tau, 1, &sp))) break;
         const int64_t mc = sp.pid ? sp.m_plain : m;   // edges the colouring covers
         const int32_t* cu = sp.pid ? sp.gu : h->u;
         const int32_t* cv = sp.pid ? sp.gv : h->v;
@@ -1146,7 +1146,7 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
                             (uint32_t)n, reinterpret_cast<uint16_t*>(h->crk));
                 cudaStreamSynchronize(st);
             }
-            dfree(&ok[0]); dfree(&ok[1]); dfree(&ov[0]); dfree(&ov[1]);
+            dfree(h, &ok[0]); dfree(h, &ok[1]); dfree(h, &ov[0]); dfree(h, &ov[1]);
             if (!good) break;
         }
         if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
@@ -1168,7 +1168,7 @@ lowd_status lowd_sweep_rederive(lowd_ctx* h, double* stats3) {
     cudaMemsetAsync(h->d_stats, 0, 3 * sizeof(double), st);
     if (h->sched == 2) {
         lowd_status r = lowd_stream_rederive(h, L64);
-        if (r != LOWD_OK) { dfree(&L64); return r; }
+        if (r != LOWD_OK) { dfree(h, &L64); return r; }
     } else if (h->m_pad > 0) {
         LOWD_LAUNCH(k_rederive, grid_for(h->m_pad), kT, 0, st, h->m_pad, h->cuv, h->cw, h->cs, L64);
     }
@@ -1177,7 +1177,7 @@ lowd_status lowd_sweep_rederive(lowd_ctx* h, double* stats3) {
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(tmp3, h->d_stats, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    dfree(&L64);
+    dfree(h, &L64);
     if (e != cudaSuccess) return h->fail(e);
     if (stats3) { stats3[0] = tmp3[0]; stats3[1] = tmp3[1]; stats3[2] = tmp3[2]; }
     return LOWD_OK;
@@ -1210,8 +1210,8 @@ lowd_status lowd_sweep_edge_order(lowd_ctx* h, int32_t* out_dev) {
         if (cudaGetLastError() != cudaSuccess) s = h->fail(cudaGetLastError());
     }
     cudaStreamSynchronize(h->st);
-    dfree(&f);
-    dfree(&pos);
+    dfree(h, &f);
+    dfree(h, &pos);
     return s;
 }
 

@@ -128,6 +128,13 @@ def test_auto_hub_threshold_closed_forms(oracle_mod):
     # a path: all degrees <= 2; 2^1 = 2 has n - 2 nodes of degree 2 > 1; 4 has none
     g = synth.small_family("path", 20)
     assert oracle_mod.auto_hub_threshold(g.n, g.u, g.v) == 4
+    # schedule 1: the smallest power of two >= half the maximum degree
+    g = synth.small_family("star", 30)                     # max degree 29: 16 (2 * 16 >= 29)
+    assert oracle_mod.auto_hub_threshold(g.n, g.u, g.v, schedule=1) == 16
+    g = synth.small_family("clique", 6)                    # max degree 5: 4
+    assert oracle_mod.auto_hub_threshold(g.n, g.u, g.v, schedule=1) == 4
+    g = synth.small_family("path", 20)                     # max degree 2: the minimum, 2
+    assert oracle_mod.auto_hub_threshold(g.n, g.u, g.v, schedule=1) == 2
 
 
 @pytest.mark.parametrize("gi", range(2))
