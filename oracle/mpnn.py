@@ -7,8 +7,9 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/`` and never by the library.  Plai
 float64; the forward pass, the loss and the backward pass follow the definitions below
 term by term, with no fusion.  With ``bf16=True`` the values the GPU stores in bfloat16
 (weights of the message-passing layers, node states h and means m, the layer gradients fed
-to the tensor cores) are rounded to bfloat16 (round to nearest even, through float32) at
-the same points; the backward pass treats those roundings as the identity, as the GPU does.
+to the tensor cores in the backward-data and weight-gradient products) are rounded to
+bfloat16 (round to nearest even, through float32) at the same points; the backward pass
+treats those roundings as the identity, as the GPU does.
 
 Network (hidden width H = 64, L = 3 message-passing layers) on an undirected graph with
 edges e = (lo, hi), lo < hi, weights w_e > 0; N(v) are v's neighbours, deg(v) = |N(v)|:
@@ -167,7 +168,7 @@ def backward(params, fw):
         hl = fw["h"][l + 1]
         dA = G * (hl > 0)
         X = np.concatenate([fw["h"][l], fw["m"][l]], axis=1)
-        dWs[l] = (X.T @ dA).T                              # [out][in]
+        dWs[l] = (X.T @ rb(dA)).T                          # [out][in]; dA enters the tensor cores
         dbs[l] = dA.sum(axis=0)
         dX = rb(dA) @ rb(Ws[l])
         dH, dM = dX[:, :H], dX[:, H:]
