@@ -352,7 +352,7 @@ lowd_status lowd_get_info(lowd_handle h, lowd_info* info) {
     x.pruned = h->pruned;
     x.classes = h->C + h->star_S;
     x.schedule = h->sched;
-    x.max_degree = h->max_deg;
+    x.max_degree = lowd_max_degree(h);
     x.prune_rounds = h->prune_rounds;
     x.sweep_kernel = h->sweep_kernel;
     x.sweep_edges_per_thread = h->sweep_E;

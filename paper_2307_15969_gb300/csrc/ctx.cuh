@@ -37,7 +37,7 @@ struct lowd_ctx {
     float* w = nullptr;     // [m] weights, null for unit weights
     int64_t* wu = nullptr;  // [m] weight units of 2^-20, null for unit weights
     int32_t* map = nullptr; // [n] current id -> original id; null while current == G
-    int32_t max_deg = 0;
+    int32_t max_deg = -1;      // maximum unweighted degree of the current graph; -1: not computed yet
 
     // pruning record (original numbering)
     int pruned = 0;
@@ -164,6 +164,7 @@ lowd_status lowd_graph_load(lowd_ctx* h, const int32_t* du, const int32_t* dv, c
                             int64_t m_in);
 lowd_status lowd_graph_prune(lowd_ctx* h, int32_t* rounds);
 lowd_status lowd_graph_max_degree(lowd_ctx* h);
+int32_t lowd_max_degree(lowd_ctx* h);   // h->max_deg, computed on first use
 
 // sweep.cu
 lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_splits_canon);

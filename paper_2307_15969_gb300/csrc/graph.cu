@@ -16,7 +16,6 @@ using namespace lowd;
 namespace {
 
 constexpr int kT = 256;
-constexpr double kUnit = 1048576.0;  // 2^20 weight units per 1.0
 
 
 enum { ERR_RANGE = 1, ERR_LOOP = 2, ERR_WEIGHT = 4, ERR_GRID = 8, UNSORTED = 16 };
@@ -24,6 +23,31 @@ enum { ERR_RANGE = 1, ERR_LOOP = 2, ERR_WEIGHT = 4, ERR_GRID = 8, UNSORTED = 16 
 // One pass over the input pairs: range, loop and weight checks, and whether the input is
 // already strictly increasing in the canonical key lo * n + hi; with keys != null the keys
 // (and the input position of each) are written for the sort.
+// Weight units with integer arithmetic only (FP64 is slow on this GPU): rint(x * 2^20) for
+// a finite x > 0, at least 1.  x = m 2^(e - 150) with a 24-bit integer m, so x 2^20 =
+// m 2^(e - 130): a left shift, or a right shift rounded to nearest, ties to even.
+__device__ __forceinline__ int64_t weight_units(float x) {
+    const uint32_t bits = __float_as_uint(x);
+    const int ex = (int)((bits >> 23) & 0xffu);
+    if (ex == 0) return 1;   // subnormal: x 2^20 < 1
+    const uint64_t m = (uint64_t)((bits & 0x7fffffu) | 0x800000u);
+    const int sh = ex - 130;
+    if (sh >= 0) return sh >= 39 ? INT64_MAX : (int64_t)(m << sh);
+    const int r = -sh;
+    if (r > 25) return 1;    // x 2^20 < 1/2: rounds to 0
+    const uint64_t q = m >> r, rem = m & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+    const uint64_t y = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+    return y < 1ull ? 1 : (int64_t)y;
+}
+
+// x 2^20 is an integer (the weight lies on the 2^-20 grid); the product by a power of two is
+// exact in FP32 unless it overflows, and an infinite product counts as on the grid, as the
+// FP64 product (then a huge integer) would
+__device__ __forceinline__ bool on_grid(float x) {
+    const float y = x * 1048576.0f;
+    return y == rintf(y);
+}
+
 __global__ void k_check_keys(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
                              const float* __restrict__ w, int64_t m, int32_t n,
                              uint64_t* __restrict__ keys, uint32_t* __restrict__ idx,
@@ -47,13 +71,72 @@ __global__ void k_check_keys(const int32_t* __restrict__ u, const int32_t* __res
         if (w) {
             float x = w[e];
             if (!(x > 0.0f) || !isfinite(x)) flags |= ERR_WEIGHT;
-            double y = (double)x * kUnit;
-            if (y != rint(y)) flags |= ERR_GRID;
+            if (!on_grid(x)) flags |= ERR_GRID;
         }
         if (e > 0) {
             int32_t pa = u[e - 1], pb = v[e - 1];
             if (pa >= 0 && pa < n && pb >= 0 && pb < n) {
                 uint64_t pk = (uint64_t)min(pa, pb) * (uint64_t)n + (uint64_t)max(pa, pb);
+                if (!(pk < k)) flags |= UNSORTED;
+            }
+        }
+    }
+    flags = __reduce_or_sync(0xffffffffu, flags);
+    if (flags && lane_id() == 0) atomicOr(err, flags);
+}
+
+// The same checks when no keys are wanted (first look at an input), four edges per thread
+// with 16-byte loads (u, v and w 16-byte aligned), the tail edges one per thread.
+__device__ __forceinline__ int check_one(int32_t a, int32_t b, bool hw, float x, int32_t n, bool& valid,
+                                         uint64_t& k) {
+    int f = 0;
+    valid = a >= 0 && a < n && b >= 0 && b < n;
+    if (!valid) return ERR_RANGE;
+    if (a == b) f |= ERR_LOOP;
+    k = (uint64_t)min(a, b) * (uint64_t)n + (uint64_t)max(a, b);
+    if (hw) {
+        if (!(x > 0.0f) || !isfinite(x)) f |= ERR_WEIGHT;
+        if (!on_grid(x)) f |= ERR_GRID;
+    }
+    return f;
+}
+
+__global__ void k_check_vec4(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                             const float* __restrict__ w, int64_t m, int32_t n, int32_t* __restrict__ err) {
+    int flags = 0;
+    const int64_t m4 = m >> 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m4; q += stride) {
+        const int4 a4 = __ldcs(reinterpret_cast<const int4*>(u) + q);
+        const int4 b4 = __ldcs(reinterpret_cast<const int4*>(v) + q);
+        const float4 w4 = w ? __ldcs(reinterpret_cast<const float4*>(w) + q) : make_float4(1.f, 1.f, 1.f, 1.f);
+        const int32_t aa[4] = {a4.x, a4.y, a4.z, a4.w}, bb[4] = {b4.x, b4.y, b4.z, b4.w};
+        const float ww[4] = {w4.x, w4.y, w4.z, w4.w};
+        bool pvalid = false;
+        uint64_t pk = 0;
+        if (q > 0) {
+            const int32_t pa = u[4 * q - 1], pb = v[4 * q - 1];
+            pvalid = pa >= 0 && pa < n && pb >= 0 && pb < n;
+            pk = pvalid ? (uint64_t)min(pa, pb) * (uint64_t)n + (uint64_t)max(pa, pb) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            bool valid;
+            uint64_t k = 0;
+            flags |= check_one(aa[j], bb[j], w != nullptr, ww[j], n, valid, k);
+            if (valid && pvalid && !(pk < k)) flags |= UNSORTED;
+            pvalid = valid;
+            pk = k;
+        }
+    }
+    for (int64_t e = 4 * m4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        bool valid;
+        uint64_t k = 0;
+        flags |= check_one(u[e], v[e], w != nullptr, w ? w[e] : 1.0f, n, valid, k);
+        if (valid && e > 0) {
+            const int32_t pa = u[e - 1], pb = v[e - 1];
+            if (pa >= 0 && pa < n && pb >= 0 && pb < n) {
+                const uint64_t pk = (uint64_t)min(pa, pb) * (uint64_t)n + (uint64_t)max(pa, pb);
                 if (!(pk < k)) flags |= UNSORTED;
             }
         }
@@ -83,8 +166,7 @@ __global__ void k_emit_unique(const uint64_t* __restrict__ keys, const uint32_t*
         if (w_in) {
             float x = w_in[idx[i]];
             w[p] = x;
-            double y = rint((double)x * kUnit);
-            wu[p] = y < 1.0 ? 1 : (int64_t)y;
+            wu[p] = weight_units(x);
         }
     }
 }
@@ -110,32 +192,37 @@ __global__ void k_emit_sorted(const int32_t* __restrict__ du, const int32_t* __r
         if (w_in) {
             const float x = w_in[e];
             w[e] = x;
-            const double y = rint((double)x * kUnit);
-            wu[e] = y < 1.0 ? 1 : (int64_t)y;
+            wu[e] = weight_units(x);
         }
     }
 }
 
 // Weighted degree in units (unit weights count 1 per edge) and unweighted degree.
-__global__ void k_degrees(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
-                          const int64_t* __restrict__ wu, int64_t m,
-                          unsigned long long* __restrict__ deg, int32_t* __restrict__ cnt) {
+// Degrees of the handle's graph, whose edges are sorted by their low end (canonical order,
+// kept by pruning): a warp's low ends form runs of equal nodes, so each run adds its total
+// with one atomic from its last lane (a segmented sum by shuffles, no match); the high ends
+// are distinct within a run and take one atomic each.  T = int32 counts or u64 weight units.
+template <class T>
+__global__ void k_degrees_sorted(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                                 const int64_t* __restrict__ wu, int64_t m, T* __restrict__ deg) {
+    const unsigned lane = lane_id();
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = base + threadIdx.x;
         const bool ok = e < m;
-        const int32_t a = ok ? u[e] : -1, b = ok ? v[e] : -1;
-        if (cnt) {
-            warp_add<int32_t>(cnt, a, 1);
-            warp_add<int32_t>(cnt, b, 1);
+        const int32_t a = ok ? u[e] : -1;
+        const int32_t b = ok ? v[e] : -1;
+        const T x = ok ? (wu ? (T)wu[e] : (T)1) : (T)0;
+        if (ok) atomicAdd(&deg[b], x);
+        // inclusive segmented sum over runs of equal a (runs are contiguous: u is sorted)
+        T s = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, s, o);
+            const int32_t ay = __shfl_up_sync(0xffffffffu, a, o);
+            if ((int)lane >= o && ay == a) s += y;
         }
-        if (deg) {
-            if (wu) {   // weights differ per edge: one atomic per end
-                if (ok) { atomicAdd(&deg[a], (unsigned long long)wu[e]); atomicAdd(&deg[b], (unsigned long long)wu[e]); }
-            } else {
-                warp_add<unsigned long long>(deg, a, 1ull);
-                warp_add<unsigned long long>(deg, b, 1ull);
-            }
-        }
+        const int32_t an = __shfl_down_sync(0xffffffffu, a, 1);
+        if (ok && (lane == 31 || an != a)) atomicAdd(&deg[a], s);
     }
 }
 
@@ -177,17 +264,22 @@ __device__ __forceinline__ bool below_bound(unsigned long long d, int64_t N, int
 }
 
 // Round r of Algorithm 2, node side: among the listed live nodes, mark every node whose
-// current degree is below the density bound; count them.  keep[i] = 1 for survivors.
+// current degree is below the density bound (its removal round, and its bit in the removed
+// set); count them.  keep[i] = 1 for survivors.
 __global__ void k_prune_mark(const int32_t* __restrict__ act, int64_t nact,
                              const unsigned long long* __restrict__ deg, int64_t N, int64_t W,
-                             int32_t r, int32_t* __restrict__ rr, int32_t* __restrict__ keep,
-                             unsigned long long* __restrict__ removed) {
+                             int32_t r, int32_t* __restrict__ rr, uint32_t* __restrict__ dead,
+                             int32_t* __restrict__ keep, unsigned long long* __restrict__ removed) {
     unsigned long long c = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nact;
          i += (int64_t)gridDim.x * blockDim.x) {
         int32_t x = act[i];
         bool rem = below_bound(deg[x], N, W);
-        if (rem) { rr[x] = r; ++c; }
+        if (rem) {
+            rr[x] = r;
+            atomicOr(&dead[x >> 5], 1u << (x & 31));
+            ++c;
+        }
         keep[i] = rem ? 0 : 1;
     }
     c = warp_sum(c);
@@ -196,21 +288,27 @@ __global__ void k_prune_mark(const int32_t* __restrict__ act, int64_t nact,
 
 // Round r, edge side: every live edge with an end removed in this round takes its weight
 // off W(H) and off the degree of a surviving end; edges with both ends alive go to the next
-// round's edge list (in any order: the list only drives the rounds).  A block takes tiles of
-// kPruneTile edges and reserves room for a tile's survivors with one atomic; unit-weight
-// decrements are aggregated per warp on equal nodes.
+// round's edge list (in any order: the list only drives the rounds).  The live list holds
+// only edges whose ends were alive before this round, so an end is removed in this round
+// exactly when its bit in the removed set is on (a 1-bit-per-node set: far fewer cache lines
+// than the removal rounds).  A block takes tiles of kPruneTile edges and reserves room for a
+// tile's survivors with one atomic; unit-weight decrements are aggregated per warp on equal
+// nodes.
 constexpr int kPruneItems = 8;
 constexpr int kPruneTile = kT * kPruneItems;
 
 __global__ void __launch_bounds__(kT)
 k_prune_edges(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
-              const int64_t* __restrict__ ew, int64_t me, int32_t r,
-              const int32_t* __restrict__ rr, unsigned long long* __restrict__ deg,
+              const int64_t* __restrict__ ew, int64_t me, const uint32_t* __restrict__ dead,
+              unsigned long long* __restrict__ deg,
               unsigned long long* __restrict__ removedW,
               int32_t* __restrict__ nu, int32_t* __restrict__ nv,
               int64_t* __restrict__ nw, unsigned long long* __restrict__ ncount) {
     __shared__ unsigned long long sh_base;
-    __shared__ int32_t sh_scan[kT / 32 + 1];
+    __shared__ int32_t sh_warp[kT / 32];
+    const unsigned lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    const int warp = (int)(threadIdx.x >> 5);
     unsigned long long acc = 0;
     for (int64_t tb = (int64_t)blockIdx.x * kPruneTile; tb < me; tb += (int64_t)gridDim.x * kPruneTile) {
         int32_t a[kPruneItems], b[kPruneItems];
@@ -223,7 +321,8 @@ k_prune_edges(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
             a[i] = ok ? eu[e] : -1;
             b[i] = ok ? ev[e] : -1;
             x[i] = ok ? (ew ? ew[e] : 1) : 0;
-            const bool ra = ok && rr[a[i]] == r, rb = ok && rr[b[i]] == r;
+            const bool ra = ok && ((__ldg(dead + (a[i] >> 5)) >> (a[i] & 31)) & 1u);
+            const bool rb = ok && ((__ldg(dead + (b[i] >> 5)) >> (b[i] & 31)) & 1u);
             if (ra || rb) acc += (unsigned long long)x[i];
             const int32_t da = (ok && rb && !ra) ? a[i] : -1;   // surviving end of a removed edge
             const int32_t db = (ok && ra && !rb) ? b[i] : -1;
@@ -236,19 +335,32 @@ k_prune_edges(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
             }
             if (ok && !ra && !rb) keepm |= 1u << i;
         }
-        int32_t total = 0;
-        const int32_t off = block_excl_scan<int32_t>(__popc(keepm), sh_scan, &total);
-        if (threadIdx.x == 0) sh_base = total ? atomicAdd(ncount, (unsigned long long)total) : 0ull;
-        __syncthreads();
-        unsigned long long p = sh_base + (unsigned long long)off;
-        __syncthreads();   // sh_base is rewritten by the next tile
+        // survivors: each warp writes item i of its lanes as one contiguous run (coalesced)
+        unsigned bal[kPruneItems];
+        int32_t wcnt = 0;
 #pragma unroll
         for (int i = 0; i < kPruneItems; ++i) {
-            if (keepm & (1u << i)) {
-                nu[p] = a[i]; nv[p] = b[i];
-                if (nw) nw[p] = x[i];
-                ++p;
+            bal[i] = __ballot_sync(0xffffffffu, (keepm >> i) & 1u);
+            wcnt += __popc(bal[i]);
+        }
+        if (lane == 0) sh_warp[warp] = wcnt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t t = 0;
+            for (int w = 0; w < kT / 32; ++w) { const int32_t c = sh_warp[w]; sh_warp[w] = t; t += c; }
+            sh_base = t ? atomicAdd(ncount, (unsigned long long)t) : 0ull;
+        }
+        __syncthreads();
+        unsigned long long p = sh_base + (unsigned long long)sh_warp[warp];
+        __syncthreads();   // sh_base and sh_warp are rewritten by the next tile
+#pragma unroll
+        for (int i = 0; i < kPruneItems; ++i) {
+            if ((keepm >> i) & 1u) {
+                const unsigned long long q = p + __popc(bal[i] & lt);
+                nu[q] = a[i]; nv[q] = b[i];
+                if (nw) nw[q] = x[i];
             }
+            p += __popc(bal[i]);
         }
     }
     acc = warp_sum(acc);
@@ -276,25 +388,91 @@ __global__ void k_node_map(const int32_t* __restrict__ keep, const int32_t* __re
         if (keep[i]) map[pos[i]] = old_map ? old_map[i] : (int32_t)i;
 }
 
-__global__ void k_keep_edges(const int32_t* __restrict__ u, const int32_t* __restrict__ v, int64_t m,
-                             const int32_t* __restrict__ keepn, int32_t* __restrict__ keepe) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x)
-        keepe[e] = (keepn[u[e]] && keepn[v[e]]) ? 1 : 0;
+// Stable compaction of G's edges to H (both ends alive), by tiles of kPruneTile edges in
+// index order (item i of thread t is edge tile + i kT + t): the first pass counts each
+// tile's survivors, a scan of the counts gives each tile's output start, and the second pass
+// recomputes the survivors and writes them in index order, positions from per-(item, warp)
+// ballots.
+__device__ __forceinline__ bool node_dead(const uint32_t* __restrict__ dead, int32_t x) {
+    return (__ldg(dead + (x >> 5)) >> (x & 31)) & 1u;
 }
 
-__global__ void k_emit_edges(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
-                             const float* __restrict__ w, const int64_t* __restrict__ wu, int64_t m,
-                             const int32_t* __restrict__ keepe, const int32_t* __restrict__ epos,
-                             const int32_t* __restrict__ npos, int32_t* __restrict__ ou,
-                             int32_t* __restrict__ ov, float* __restrict__ ow, int64_t* __restrict__ owu) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        if (!keepe[e]) continue;
-        int32_t p = epos[e];
-        ou[p] = npos[u[e]];
-        ov[p] = npos[v[e]];
-        if (w) { ow[p] = w[e]; owu[p] = wu[e]; }
+__global__ void __launch_bounds__(kT) k_tile_keep_counts(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                                                         int64_t m, const uint32_t* __restrict__ dead,
+                                                         int32_t* __restrict__ tcnt) {
+    __shared__ int32_t sh[kT / 32];
+    const int64_t tiles = (m + kPruneTile - 1) / kPruneTile;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        int32_t a[kPruneItems], b[kPruneItems];
+#pragma unroll
+        for (int i = 0; i < kPruneItems; ++i) {   // loads first, no branches between them
+            const int64_t e = t * kPruneTile + (int64_t)i * kT + threadIdx.x;
+            a[i] = e < m ? u[e] : 0;
+            b[i] = e < m ? v[e] : 0;
+        }
+        int32_t c = 0;
+#pragma unroll
+        for (int i = 0; i < kPruneItems; ++i) {
+            const int64_t e = t * kPruneTile + (int64_t)i * kT + threadIdx.x;
+            c += (int32_t)((e < m) & !node_dead(dead, a[i]) & !node_dead(dead, b[i]));
+        }
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane_id() == 0) sh[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t tot = 0;
+            for (int w = 0; w < kT / 32; ++w) tot += sh[w];
+            tcnt[t] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kT) k_tile_emit(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                                                  const float* __restrict__ w, const int64_t* __restrict__ wu,
+                                                  int64_t m, const uint32_t* __restrict__ dead,
+                                                  const int32_t* __restrict__ tpos, const int32_t* __restrict__ npos,
+                                                  int32_t* __restrict__ ou, int32_t* __restrict__ ov,
+                                                  float* __restrict__ ow, int64_t* __restrict__ owu) {
+    __shared__ int32_t pre[kPruneItems][kT / 32];
+    const int warp = (int)(threadIdx.x >> 5);
+    const unsigned lt = (1u << lane_id()) - 1u;
+    const int64_t tiles = (m + kPruneTile - 1) / kPruneTile;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        int32_t a[kPruneItems], b[kPruneItems];
+        unsigned bal[kPruneItems];
+#pragma unroll
+        for (int i = 0; i < kPruneItems; ++i) {   // loads first, no branches between them
+            const int64_t e = t * kPruneTile + (int64_t)i * kT + threadIdx.x;
+            a[i] = e < m ? u[e] : 0;
+            b[i] = e < m ? v[e] : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < kPruneItems; ++i) {
+            const int64_t e = t * kPruneTile + (int64_t)i * kT + threadIdx.x;
+            const bool keep = (e < m) & !node_dead(dead, a[i]) & !node_dead(dead, b[i]);
+            bal[i] = __ballot_sync(0xffffffffu, keep);
+            if (lane_id() == 0) pre[i][warp] = __popc(bal[i]);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {   // exclusive prefix in index order: item-major, then warp
+            int32_t run = 0;
+            for (int i = 0; i < kPruneItems; ++i)
+                for (int q = 0; q < kT / 32; ++q) { const int32_t c = pre[i][q]; pre[i][q] = run; run += c; }
+        }
+        __syncthreads();
+        const int32_t base = tpos[t];
+#pragma unroll
+        for (int i = 0; i < kPruneItems; ++i) {
+            if ((bal[i] >> lane_id()) & 1u) {
+                const int64_t e = t * kPruneTile + (int64_t)i * kT + threadIdx.x;
+                const int32_t p = base + pre[i][warp] + __popc(bal[i] & lt);
+                ou[p] = npos[a[i]];
+                ov[p] = npos[b[i]];
+                if (w) { ow[p] = w[e]; owu[p] = wu[e]; }
+            }
+        }
+        __syncthreads();   // pre is rewritten by the next tile
     }
 }
 
@@ -331,8 +509,12 @@ lowd_status lowd_graph_load(lowd_ctx* h, const int32_t* du, const int32_t* dv, c
         if (cudaMallocHost(&h->h_pin, 16 * sizeof(int64_t)) != cudaSuccess) { s = h->fail(cudaErrorMemoryAllocation); break; }
         cudaMemsetAsync(h->d_i32, 0, 16 * sizeof(int32_t), st);
         if (m_in > 0) {   // checks only: keys are written only if the input needs sorting
-            LOWD_LAUNCH(k_check_keys, grid_for(m_in), kT, 0, st, du, dv, dw, m_in, n, (uint64_t*)nullptr,
-                        (uint32_t*)nullptr, h->d_i32);
+            const bool a16 = ((uintptr_t)du & 15) == 0 && ((uintptr_t)dv & 15) == 0 && ((uintptr_t)dw & 15) == 0;
+            if (a16)
+                LOWD_LAUNCH(k_check_vec4, grid_for((m_in + 3) / 4), kT, 0, st, du, dv, dw, m_in, n, h->d_i32);
+            else
+                LOWD_LAUNCH(k_check_keys, grid_for(m_in), kT, 0, st, du, dv, dw, m_in, n, (uint64_t*)nullptr,
+                            (uint32_t*)nullptr, h->d_i32);
         }
         if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
         int32_t err = 0;
@@ -386,10 +568,15 @@ lowd_status lowd_graph_load(lowd_ctx* h, const int32_t* du, const int32_t* dv, c
             LOWD_LAUNCH(k_emit_unique, grid_for(m_in), kT, 0, st, keys[cur], idx[cur], first, pos, m_in, n, dw,
                         h->u, h->v, h->w, h->wu);
         if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
-        s = lowd_graph_max_degree(h);
+        h->max_deg = -1;   // computed when first needed (lowd_max_degree): pruning does not need G's
     } while (0);
     cleanup();
     return s;
+}
+
+int32_t lowd_max_degree(lowd_ctx* h) {
+    if (h->max_deg < 0 && lowd_graph_max_degree(h) != LOWD_OK) return h->n > 0 ? h->n - 1 : 0;   // an upper bound
+    return h->max_deg;
 }
 
 lowd_status lowd_graph_max_degree(lowd_ctx* h) {
@@ -398,7 +585,7 @@ lowd_status lowd_graph_max_degree(lowd_ctx* h) {
     LOWD_TRY(dalloc(h, &cnt, h->n));
     cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)h->n, st);
     cudaMemsetAsync(h->d_i32 + 2, 0, sizeof(int32_t), st);
-    if (h->m > 0) LOWD_LAUNCH(k_degrees, grid_for(h->m), kT, 0, st, h->u, h->v, nullptr, h->m, nullptr, cnt);
+    if (h->m > 0) LOWD_LAUNCH(k_degrees_sorted<int32_t>, grid_for(h->m), kT, 0, st, h->u, h->v, nullptr, h->m, cnt);
     LOWD_LAUNCH(k_max_i32, grid_for(h->n), kT, 0, st, cnt, h->n, h->d_i32 + 2);
     int32_t md = 0;
     cudaError_t e = cudaMemcpyAsync(&md, h->d_i32 + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
@@ -422,6 +609,7 @@ lowd_status lowd_graph_prune(lowd_ctx* h, int32_t* rounds_out) {
     int32_t *eu[2] = {nullptr, nullptr}, *ev[2] = {nullptr, nullptr};
     int64_t* ew[2] = {nullptr, nullptr};
     int32_t *keepe = nullptr, *epos = nullptr, *nmap = nullptr;
+    uint32_t* dead = nullptr;   // nodes removed so far, one bit each
     int32_t *nu = nullptr, *nv = nullptr;
     float* nw = nullptr;
     int64_t* nwu = nullptr;
@@ -430,7 +618,7 @@ lowd_status lowd_graph_prune(lowd_ctx* h, int32_t* rounds_out) {
         dfree(h, &deg); dfree(h, &dkey[0]); dfree(h, &dkey[1]); dfree(h, &dval[0]); dfree(h, &dval[1]);
         dfree(h, &act); dfree(h, &act2); dfree(h, &keep); dfree(h, &pos);
         dfree(h, &eu[0]); dfree(h, &eu[1]); dfree(h, &ev[0]); dfree(h, &ev[1]); dfree(h, &ew[0]); dfree(h, &ew[1]);
-        dfree(h, &keepe); dfree(h, &epos); dfree(h, &nmap); dfree(h, &nu); dfree(h, &nv); dfree(h, &nw); dfree(h, &nwu);
+        dfree(h, &keepe); dfree(h, &epos); dfree(h, &nmap); dfree(h, &dead); dfree(h, &nu); dfree(h, &nv); dfree(h, &nw); dfree(h, &nwu);
     };
     do {
         if ((s = dalloc(h, &deg, n))) break;
@@ -438,7 +626,8 @@ lowd_status lowd_graph_prune(lowd_ctx* h, int32_t* rounds_out) {
         if ((s = dalloc(h, &h->removal_round, n))) break;
         if ((s = h->need_tmp(lowd_sort_tmp_bytes(m > n ? m : n)))) break;
         cudaMemsetAsync(deg, 0, sizeof(unsigned long long) * (size_t)n, st);
-        if (m > 0) LOWD_LAUNCH(k_degrees, grid_for(m), kT, 0, st, h->u, h->v, h->wu, m, deg, nullptr);
+        if (m > 0)
+            LOWD_LAUNCH(k_degrees_sorted<unsigned long long>, grid_for(m), kT, 0, st, h->u, h->v, h->wu, m, deg);
         // W(G) = sum of degrees / 2 = sum of weights (units)
         unsigned long long* dmax = (unsigned long long*)(h->d_i64 + 0);
         cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), st);
@@ -471,6 +660,8 @@ lowd_status lowd_graph_prune(lowd_ctx* h, int32_t* rounds_out) {
             W = m;
         }
         int64_t N = n;
+        if ((s = dalloc(h, &dead, ((size_t)n + 31) / 32))) break;
+        cudaMemsetAsync(dead, 0, sizeof(uint32_t) * (((size_t)n + 31) / 32), st);
 
         // live node list (degree order) and live edge list
         if ((s = dalloc(h, &act, n))) break;
@@ -494,10 +685,10 @@ lowd_status lowd_graph_prune(lowd_ctx* h, int32_t* rounds_out) {
         while (N > 0) {
             int32_t rnext = r + 1;
             cudaMemsetAsync(h->d_i64 + 4, 0, 3 * sizeof(int64_t), st);
-            LOWD_LAUNCH(k_prune_mark, grid_for(nact), kT, 0, st, act, nact, deg, N, W, rnext, h->removal_round, keep, removed);
+            LOWD_LAUNCH(k_prune_mark, grid_for(nact), kT, 0, st, act, nact, deg, N, W, rnext, h->removal_round, dead,
+                        keep, removed);
             if (me > 0)
-                LOWD_LAUNCH(k_prune_edges, lowd_grid_for(me, kPruneTile, 4), kT, 0, st, cu_, cv_, cw_, me, rnext,
-                            h->removal_round, deg,
+                LOWD_LAUNCH(k_prune_edges, lowd_grid_for(me, kPruneTile, 4), kT, 0, st, cu_, cv_, cw_, me, dead, deg,
                                                            removedW, eu[nxt], ev[nxt], ew[nxt], ncount);
             if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
             if (cudaMemcpyAsync(h->h_pin, h->d_i64 + 4, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -522,26 +713,28 @@ lowd_status lowd_graph_prune(lowd_ctx* h, int32_t* rounds_out) {
         if (s) break;
         h->prune_rounds = r;
 
-        // compaction to H: survivors by ascending id, edges in original order
-        if ((s = dalloc(h, &keepe, m))) break;
-        if ((s = dalloc(h, &epos, m))) break;
+        // compaction to H: survivors by ascending id, edges in original order (the live list
+        // of the last round has exactly H's edges: me of them)
+        const int64_t tiles = (m + kPruneTile - 1) / kPruneTile;
+        if ((s = dalloc(h, &keepe, tiles))) break;   // survivors per tile
+        if ((s = dalloc(h, &epos, tiles))) break;    // their output start
         if ((s = dalloc(h, &nmap, N))) break;
         LOWD_LAUNCH(k_keep_nodes, grid_for(n), kT, 0, st, h->removal_round, n, keep);
         scan_exclusive<int32_t>(keep, pos, n, nullptr, h->tmp, st);
         LOWD_LAUNCH(k_node_map, grid_for(n), kT, 0, st, keep, pos, n, h->map, nmap);
-        if (m > 0) LOWD_LAUNCH(k_keep_edges, grid_for(m), kT, 0, st, h->u, h->v, m, keep, keepe);
-        scan_exclusive<int32_t>(keepe, epos, m, h->d_i32 + 4, h->tmp, st);
-        if (cudaMemcpyAsync(h->h_pin, h->d_i32 + 4, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
-        int64_t mH = *(int32_t*)h->h_pin;
+        const int64_t mH = me;
         if ((s = dalloc(h, &nu, mH))) break;
         if ((s = dalloc(h, &nv, mH))) break;
         if (h->w) {
             if ((s = dalloc(h, &nw, mH))) break;
             if ((s = dalloc(h, &nwu, mH))) break;
         }
-        if (m > 0)
-            LOWD_LAUNCH(k_emit_edges, grid_for(m), kT, 0, st, h->u, h->v, h->w, h->wu, m, keepe, epos, pos, nu, nv, nw, nwu);
+        if (m > 0) {
+            const unsigned gt = lowd_grid_for(m, kPruneTile, 4);
+            LOWD_LAUNCH(k_tile_keep_counts, gt, kT, 0, st, h->u, h->v, m, dead, keepe);
+            scan_exclusive<int32_t>(keepe, epos, tiles, nullptr, h->tmp, st);
+            LOWD_LAUNCH(k_tile_emit, gt, kT, 0, st, h->u, h->v, h->w, h->wu, m, dead, epos, pos, nu, nv, nw, nwu);
+        }
         if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
         // swap in H
         dfree(h, &h->u); dfree(h, &h->v); dfree(h, &h->w); dfree(h, &h->wu); dfree(h, &h->map);

@@ -558,7 +558,8 @@ lowd_status lowd_star_split(lowd_ctx* h, int32_t hub_tau, int schedule, StarSpli
         int32_t tau = hub_tau;
         if (tau == 1 && schedule == 1) {   // the near-universal nodes: degree >= ~max degree / 2
             int64_t p = 2;
-            while (2 * p < (int64_t)h->max_deg && p < (1 << 30)) p *= 2;
+            const int64_t dmax = lowd_max_degree(h);
+            while (2 * p < dmax && p < (1 << 30)) p *= 2;
             tau = (int32_t)p;
         } else if (tau == 1) {
             if ((s = dalloc(h, &cnt, 32))) break;
@@ -640,7 +641,8 @@ lowd_status lowd_star_blocks(lowd_ctx* h, const StarSplit& sp, int64_t p0, int32
             if (which == 2 && c) { uint32_t* t = sk0; sk0 = sk1; sk1 = t; }   // leaf keys in sk0
         }
         LOWD_LAUNCH(k_star_step_keys, grid_for(ms), kT, 0, st, sk0, cur_o, ms, h->u, h->v, sp.dfull, sp.tau, q0);
-        const int sbits = 32 + bit_length_u64((uint64_t)(h->max_deg > 0 ? h->max_deg : 1));   // step < max degree
+        const int32_t dmax = lowd_max_degree(h);
+        const int sbits = 32 + bit_length_u64((uint64_t)(dmax > 0 ? dmax : 1));   // step < max degree
         const int cq = radix_sort_pairs<uint64_t, int32_t>(q0, cur_o, q1, oth_o, ms, sbits, h->tmp, st);
         uint64_t* qk = cq ? q1 : q0;
         int32_t* qo = cq ? oth_o : cur_o;

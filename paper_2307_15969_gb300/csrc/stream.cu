@@ -837,7 +837,8 @@ lowd_status lowd_stream_prepare(lowd_ctx* h, const float* init_splits_canon) {
             int32_t* vtie = val[c1];
             int32_t* vother = val[1 - c1];
             LOWD_LAUNCH(k_degree_keys, grid_for(m), kT, 0, st, vtie, m, cu, cv, deg, k64[0]);
-            const int dbits = bit_length_u64((uint64_t)(h->max_deg > 0 ? h->max_deg : 1));
+            const int32_t dmax = lowd_max_degree(h);
+            const int dbits = bit_length_u64((uint64_t)(dmax > 0 ? dmax : 1));
             int c2 = radix_sort_pairs<uint64_t, int32_t>(k64[0], vtie, k64[1], vother, m, 32 + dbits, h->tmp, st);
             ord = c2 ? vother : vtie;
             int32_t* spare = c2 ? vtie : vother;

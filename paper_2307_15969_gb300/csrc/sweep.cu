@@ -1127,7 +1127,7 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
         // ranks of every end among its node's updates in the pass order (the staged sweep
         // without class barriers); node degrees must fit 15 bits
         // (plain classes only)
-        if (m_pad_plain > 0 && h->max_deg < 0x7fff) {
+        if (m_pad_plain > 0 && lowd_max_degree(h) < 0x7fff) {
             const int64_t mq = m_pad_plain;
             uint32_t* ok[2] = {nullptr, nullptr};
             int32_t* ov[2] = {nullptr, nullptr};
