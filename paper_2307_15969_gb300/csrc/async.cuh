@@ -129,24 +129,33 @@ constexpr uint32_t kGridSpins = 1u << 24;    // bounded waits: grid barrier (wit
 // the next generation (count and gen start at zero; the counter is back at zero after every
 // barrier, so later launches reuse the words).  Bounded: on expiry bit 1 of the error word
 // is set and false is returned.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const volatile unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Arrival: an acquire-release add (publishes this block's writes, which the block barrier
+// ordered before it, and lets the last arriver see every other block's); the last arriver
+// re-arms the counter and opens the generation with a release; the others poll it with
+// acquire loads.
 __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks, int32_t* err) {
     __syncthreads();
     bool ok = true;
     if (threadIdx.x == 0) {
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(count, 1u) == nblocks - 1) {
-            *count = 0;
-            __threadfence();
-            atomicAdd((unsigned*)gen, 1u);
+        const unsigned g = ld_acquire_gpu(gen);
+        unsigned old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+        if (old == nblocks - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(count) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(gen) : "memory");
         } else {
             uint32_t spins = 0;
-            while (*gen == g) {
+            while (ld_acquire_gpu(gen) == g) {
                 if (++spins > kGridSpins) { ok = false; atomicOr(err, 2); break; }
                 if (spins > 4096) __nanosleep(64);   // poll fast at first, then back off
             }
         }
-        __threadfence();
     }
     __shared__ int okb;
     if (threadIdx.x == 0) okb = ok ? 1 : 0;

@@ -154,8 +154,9 @@ __global__ void k_set_i32(int32_t* __restrict__ x, int32_t val) { *x = val; }
 // and summed (pairwise, by TwoSum) into the hub's change, so a load stays the exact sum of
 // what moved and the star conserves the total weight.
 
-constexpr int kStarThreads = 512;
-constexpr int kStarWarps = kStarThreads / 32;
+constexpr int kStarThreads = 512;               // block of the star steps: few stars per step
+constexpr int kStarThreadsSmall = 128;          // many stars per step: more stars at once per SM
+constexpr int kStarWarps = kStarThreads / 32;   // the most warps a block has
 constexpr int kStarRegs = 8;       // edges per thread held in registers
 constexpr int kStarNewton = 64;    // iteration cap of the root search (bracketed, so it always ends)
 
@@ -257,7 +258,8 @@ __device__ __forceinline__ void block_sum(float2 (&pp)[NP], float (&f)[NF], int 
     for (int i = 0; i < NF; ++i) f[i] = 0.0f;
 #pragma unroll
     for (int i = 0; i < NI; ++i) k[i] = 0;
-    for (int w = 0; w < kStarWarps; ++w) {
+    const int nw = (int)(blockDim.x >> 5);
+    for (int w = 0; w < nw; ++w) {
 #pragma unroll
         for (int i = 0; i < NP; ++i) pair_acc(pp[i].x, pp[i].y, shf[NW * w + 2 * i], shf[NW * w + 2 * i + 1]);
 #pragma unroll
@@ -382,8 +384,8 @@ __device__ __forceinline__ void star_apply(const StarIO& io, float* cs, int32_t 
 // a_j = (l_j - frame) + t_j for a leaf load pair l_j and a frame pair
 __device__ __forceinline__ float frame_level(float2 L, float2 F, float t) { return ((L.x - F.x) + (L.y - F.y)) + t; }
 
-template <bool WEIGHTED, bool PACKED>
-__global__ void __launch_bounds__(kStarThreads)
+template <bool WEIGHTED, bool PACKED, int NT>
+__global__ void __launch_bounds__(NT, NT == kStarThreads ? 1 : 4)
 k_star_steps(int32_t S, const int32_t* __restrict__ step_seg, const int32_t* __restrict__ seg_beg,
              const int32_t* __restrict__ seg_hub, StarIO io, const float* __restrict__ cw, float* __restrict__ cs,
              float2* __restrict__ Bbuf, int32_t bbuf_p0, unsigned* __restrict__ bar, int32_t* __restrict__ err) {
@@ -702,12 +704,24 @@ cudaError_t lowd_star_pass(lowd_ctx* h) {
     if (h->star_S <= 0) return cudaSuccess;
     const bool weighted = h->cw != nullptr;
     const bool packed = h->sched == 1;
-    auto kern = weighted ? (packed ? k_star_steps<true, true> : k_star_steps<true, false>)
-                         : (packed ? k_star_steps<false, true> : k_star_steps<false, false>);
+    // many stars per step (unpruned graphs): small blocks, several stars at once per SM
+    const int sms = lowd_device_sms();
+    const bool small = (int64_t)h->star_nseg >= 2LL * sms * (int64_t)h->star_S;
+    const int nt = small ? kStarThreadsSmall : kStarThreads;
+    auto kern = small ? (weighted ? (packed ? k_star_steps<true, true, kStarThreadsSmall>
+                                            : k_star_steps<true, false, kStarThreadsSmall>)
+                                  : (packed ? k_star_steps<false, true, kStarThreadsSmall>
+                                            : k_star_steps<false, false, kStarThreadsSmall>))
+                      : (weighted ? (packed ? k_star_steps<true, true, kStarThreads>
+                                            : k_star_steps<true, false, kStarThreads>)
+                                  : (packed ? k_star_steps<false, true, kStarThreads>
+                                            : k_star_steps<false, false, kStarThreads>));
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kStarThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, 0);
     if (e != cudaSuccess) return e;
-    int blocks = lowd_device_sms() * (per_sm >= 2 ? 2 : 1);
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    const int cap = small ? 4 : 2;
+    int blocks = sms * (per_sm < cap ? per_sm : cap);
     if (h->star_maxseg < blocks) blocks = h->star_maxseg > 0 ? h->star_maxseg : 1;
     StarIO io{};
     if (packed) {
@@ -730,7 +744,7 @@ cudaError_t lowd_star_pass(lowd_ctx* h) {
     unsigned* bar = reinterpret_cast<unsigned*>(h->d_i32 + 12);
     int32_t* errp = h->d_i32 + 8;
     void* args[] = {&S, &ss, &sb, &shb, &io, &pcw, &pcs, &pbb, &bp0, &bar, &errp};
-    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kStarThreads), args, 0, h->st);
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(nt), args, 0, h->st);
     lowd_note_launch();
     return e;
 }
