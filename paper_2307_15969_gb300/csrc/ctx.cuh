@@ -165,6 +165,7 @@ lowd_status lowd_graph_load(lowd_ctx* h, const int32_t* du, const int32_t* dv, c
 lowd_status lowd_graph_prune(lowd_ctx* h, int32_t* rounds);
 lowd_status lowd_graph_max_degree(lowd_ctx* h);
 int32_t lowd_max_degree(lowd_ctx* h);   // h->max_deg, computed on first use
+void lowd_degrees_i32(lowd_ctx* h, int32_t* deg);   // unweighted degrees of the current graph
 
 // sweep.cu
 lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_splits_canon);

@@ -579,13 +579,17 @@ int32_t lowd_max_degree(lowd_ctx* h) {
     return h->max_deg;
 }
 
+void lowd_degrees_i32(lowd_ctx* h, int32_t* deg) {
+    cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)h->n, h->st);
+    if (h->m > 0) LOWD_LAUNCH(k_degrees_sorted<int32_t>, grid_for(h->m), kT, 0, h->st, h->u, h->v, nullptr, h->m, deg);
+}
+
 lowd_status lowd_graph_max_degree(lowd_ctx* h) {
     cudaStream_t st = h->st;
     int32_t* cnt = nullptr;
     LOWD_TRY(dalloc(h, &cnt, h->n));
-    cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)h->n, st);
     cudaMemsetAsync(h->d_i32 + 2, 0, sizeof(int32_t), st);
-    if (h->m > 0) LOWD_LAUNCH(k_degrees_sorted<int32_t>, grid_for(h->m), kT, 0, st, h->u, h->v, nullptr, h->m, cnt);
+    lowd_degrees_i32(h, cnt);
     LOWD_LAUNCH(k_max_i32, grid_for(h->n), kT, 0, st, cnt, h->n, h->d_i32 + 2);
     int32_t md = 0;
     cudaError_t e = cudaMemcpyAsync(&md, h->d_i32 + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st);

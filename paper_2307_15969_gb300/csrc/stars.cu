@@ -45,14 +45,6 @@ namespace {
 constexpr int kT = 256;
 inline unsigned grid_for(int64_t n) { return lowd_grid_for(n, kT); }
 
-__global__ void k_star_degrees(const int32_t* __restrict__ u, const int32_t* __restrict__ v, int64_t m,
-                               int32_t* __restrict__ deg) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-        atomicAdd(&deg[u[e]], 1);
-        atomicAdd(&deg[v[e]], 1);
-    }
-}
-
 // counts of nodes with degree >= 2^k, k = 0..30 (for the automatic threshold)
 __global__ void k_degree_powers(const int32_t* __restrict__ deg, int32_t n, unsigned long long* __restrict__ cnt) {
     __shared__ unsigned long long c[32];
@@ -555,8 +547,7 @@ lowd_status lowd_star_split(lowd_ctx* h, int32_t hub_tau, int schedule, StarSpli
     do {
         if ((s = h->need_tmp(lowd_sort_tmp_bytes(m + 2)))) break;
         if ((s = dalloc(h, &sp->dfull, n))) break;
-        cudaMemsetAsync(sp->dfull, 0, sizeof(int32_t) * (size_t)n, st);
-        LOWD_LAUNCH(k_star_degrees, grid_for(m), kT, 0, st, h->u, h->v, m, sp->dfull);
+        lowd_degrees_i32(h, sp->dfull);
         int32_t tau = hub_tau;
         if (tau == 1 && schedule == 1) {   // the near-universal nodes: degree >= ~max degree / 2
             int64_t p = 2;

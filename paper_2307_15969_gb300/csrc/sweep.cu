@@ -923,10 +923,44 @@ cudaError_t launch_sweep_tma(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* 
     return e;
 }
 
+// Ranks of every end among its node's updates in the pass order (the staged sweep without
+// class barriers), plain classes only; built on the first request for node versions.  Node
+// degrees must fit 15 bits; otherwise (or without memory) h->crk stays null and the staged
+// sweep with class barriers runs instead.
+void sweep_ranks(lowd_ctx* h) {
+    cudaStream_t st = h->st;
+    const int32_t n = h->n;
+    const int64_t mq = h->coff_h[h->C];
+    if (mq <= 0 || lowd_max_degree(h) >= 0x7fff) return;
+    uint32_t* ok[2] = {nullptr, nullptr};
+    int32_t* ov[2] = {nullptr, nullptr};
+    bool good = h->need_tmp(lowd_sort_tmp_bytes(2 * mq)) == LOWD_OK;
+    good = good && dalloc(h, &ok[0], 2 * mq) == LOWD_OK;
+    good = good && dalloc(h, &ok[1], 2 * mq) == LOWD_OK;
+    good = good && dalloc(h, &ov[0], 2 * mq) == LOWD_OK;
+    good = good && dalloc(h, &ov[1], 2 * mq) == LOWD_OK;
+    good = good && dalloc(h, &h->crk, mq) == LOWD_OK;
+    if (good) {
+        cudaMemsetAsync(h->crk, 0, sizeof(uint32_t) * (size_t)mq, st);
+        LOWD_LAUNCH(k_occurrence_keys, grid_for(mq), kT, 0, st, h->cuv, mq, ok[0], ov[0]);
+        const int cur2 = radix_sort_pairs<uint32_t, int32_t>(ok[0], ov[0], ok[1], ov[1], 2 * mq,
+                                                             bit_length_u64((uint64_t)n), h->tmp, st);
+        LOWD_LAUNCH(k_occurrence_ranks, grid_for(2 * mq), kT, 0, st, ok[cur2], ov[cur2], 2 * mq, (uint32_t)n,
+                    reinterpret_cast<uint16_t*>(h->crk));
+        if (cudaGetLastError() != cudaSuccess) dfree(h, &h->crk);
+    } else {
+        dfree(h, &h->crk);
+        cudaGetLastError();
+    }
+    dfree(h, &ok[0]); dfree(h, &ok[1]); dfree(h, &ov[0]); dfree(h, &ov[1]);
+}
+
 template <bool WEIGHTED>
 cudaError_t launch_sweep_flow(lowd_ctx* h, int32_t passes, int32_t maxlen, bool* launched) {
     *launched = false;
-    if (!h->crk || maxlen > kTmaConsumers) return cudaSuccess;
+    if (maxlen > kTmaConsumers) return cudaSuccess;
+    if (!h->crk) sweep_ranks(h);
+    if (!h->crk) return cudaSuccess;
     const size_t budget = 227 * 1024;
     constexpr int kMinStages = 3;
     int32_t G = 0, S = 0, chunk = 0;
@@ -1124,31 +1158,6 @@ lowd_status lowd_sweep_prepare(lowd_ctx* h, int schedule_req, const float* init_
         if (m_pad > 0)
             LOWD_LAUNCH(k_gather_streams, grid_for(m_pad), kT, 0, st, h->perm, m_pad, n, h->u, h->v, h->w,
                         init_splits_canon, h->cuv, h->cw, h->cs);
-        // ranks of every end among its node's updates in the pass order (the staged sweep
-        // without class barriers); node degrees must fit 15 bits
-        // (plain classes only)
-        if (m_pad_plain > 0 && lowd_max_degree(h) < 0x7fff) {
-            const int64_t mq = m_pad_plain;
-            uint32_t* ok[2] = {nullptr, nullptr};
-            int32_t* ov[2] = {nullptr, nullptr};
-            bool good = (s = h->need_tmp(lowd_sort_tmp_bytes(2 * mq))) == LOWD_OK;
-            good = good && (s = dalloc(h, &ok[0], 2 * mq)) == LOWD_OK;
-            good = good && (s = dalloc(h, &ok[1], 2 * mq)) == LOWD_OK;
-            good = good && (s = dalloc(h, &ov[0], 2 * mq)) == LOWD_OK;
-            good = good && (s = dalloc(h, &ov[1], 2 * mq)) == LOWD_OK;
-            good = good && (s = dalloc(h, &h->crk, mq)) == LOWD_OK;
-            if (good) {
-                cudaMemsetAsync(h->crk, 0, sizeof(uint32_t) * (size_t)mq, st);
-                LOWD_LAUNCH(k_occurrence_keys, grid_for(mq), kT, 0, st, h->cuv, mq, ok[0], ov[0]);
-                const int cur2 = radix_sort_pairs<uint32_t, int32_t>(ok[0], ov[0], ok[1], ov[1], 2 * mq,
-                                                                     bit_length_u64((uint64_t)n), h->tmp, st);
-                LOWD_LAUNCH(k_occurrence_ranks, grid_for(2 * mq), kT, 0, st, ok[cur2], ov[cur2], 2 * mq,
-                            (uint32_t)n, reinterpret_cast<uint16_t*>(h->crk));
-                cudaStreamSynchronize(st);
-            }
-            dfree(h, &ok[0]); dfree(h, &ok[1]); dfree(h, &ov[0]); dfree(h, &ov[1]);
-            if (!good) break;
-        }
         if (cudaGetLastError() != cudaSuccess) { s = h->fail(cudaGetLastError()); break; }
         h->sched = 1;
         h->inited = 1;

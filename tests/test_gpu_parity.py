@@ -107,6 +107,61 @@ def test_load_canonicalises_like_the_oracle(pkg, orc, device, weighted):
     pkg.lowd_free(h)
 
 
+@pytest.mark.parametrize("aligned", [True, False])
+def test_load_check_paths_on_canonical_input(pkg, orc, aligned):
+    """A canonical input takes the input check without sort keys: 16-byte aligned device
+    arrays four edges per thread (m not a multiple of 4, so the tail runs too), misaligned
+    ones (arrays that start one element into an allocation) one edge per thread.  Both must
+    accept it unchanged and reject the same bad edges and weights anywhere, tail included."""
+    import torch
+    rng = np.random.default_rng(17)
+    n = 900
+    a = rng.integers(0, n, 6000); b = rng.integers(0, n, 6000)
+    keep = a != b
+    u, v, _, _ = orc.canonicalize(n, a[keep].astype(np.int32), b[keep].astype(np.int32), None)
+    u, v = u[:1003], v[:1003]
+    m = u.shape[0]
+    assert m % 4 == 3
+    w = synth.quantise_weights(rng.lognormal(0, 1, m)).astype(np.float32)
+
+    def dev(x):
+        base = torch.zeros(x.shape[0] + 1, dtype=torch.from_numpy(x).dtype, device="cuda")
+        t = base[:x.shape[0]] if aligned else base[1:]
+        t.copy_(torch.from_numpy(x))
+        return t
+
+    def load(uu, vv, ww, flags=0):
+        return pkg.lowd_load_graph(n, dev(uu), dev(vv), None if ww is None else dev(ww), flags=flags)
+
+    h = load(u, v, w)
+    gu, gv, gw = (x.cpu().numpy() for x in pkg.lowd_get_graph(h))
+    assert np.array_equal(gu, u) and np.array_equal(gv, v) and np.array_equal(gw, w)
+    assert pkg.lowd_get_info(h)["duplicates"] == 0
+    pkg.lowd_free(h)
+    for pos in (0, 5, m - 1):
+        uu = u.copy(); uu[pos] = vv_pos = v[pos]
+        with pytest.raises(pkg.LowdError) as e:
+            load(uu, v, w)
+        assert e.value.status == pkg.LOWD_ERR_INVALID_ARG, (pos, vv_pos)
+        uu = u.copy(); uu[pos] = n
+        with pytest.raises(pkg.LowdError) as e:
+            load(uu, v, w)
+        assert e.value.status == pkg.LOWD_ERR_INVALID_ARG, pos
+        ww = w.copy(); ww[pos] = np.float32(0.1)          # off the 2^-20 grid
+        with pytest.raises(pkg.LowdError) as e:
+            load(u, v, ww)
+        assert e.value.status == pkg.LOWD_ERR_INEXACT_WEIGHTS, pos
+        h = load(u, v, ww, flags=pkg.LOWD_LOAD_ALLOW_INEXACT)
+        pkg.lowd_free(h)
+    # an out-of-order pair: the sorting path, same canonical result
+    uu, vv = u.copy(), v.copy()
+    uu[[10, 11]] = uu[[11, 10]]; vv[[10, 11]] = vv[[11, 10]]
+    h = load(uu, vv, None)
+    gu, gv, _ = (x.cpu().numpy() for x in pkg.lowd_get_graph(h))
+    assert np.array_equal(gu, u) and np.array_equal(gv, v)
+    pkg.lowd_free(h)
+
+
 def test_load_rejects_bad_input(pkg):
     g = synth.Graph(n=4, u=np.array([0, 1], np.int32), v=np.array([1, 1], np.int32), w=None)
     with pytest.raises(pkg.LowdError) as e:
