@@ -67,9 +67,9 @@ def _sweep_hash():
     return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
 
 
-def _traffic_per_pass():
-    """DRAM bytes per LOWD pass from the committed ncu summary, if it was taken on the
-    current sweep kernel source."""
+def _sweep_record():
+    """The committed ncu record of the staged sweep (DRAM bytes per pass, warp instructions
+    per class), if it was taken on the current sweep kernel source."""
     p = os.path.join(ROOT, "profiles", "k_sweep_tma_rmat22_dram.json")
     if not os.path.exists(p):
         return None
@@ -77,7 +77,12 @@ def _traffic_per_pass():
         d = json.load(f)
     if d.get("sweep_cu_sha256_16") != _sweep_hash():
         return None
-    return float(d["dram_bytes_per_pass"])
+    return d
+
+
+def _traffic_per_pass():
+    d = _sweep_record()
+    return float(d["dram_bytes_per_pass"]) if d else None
 
 
 class Clocks:
@@ -664,6 +669,10 @@ def main():
 
     achieved = BYTES_PER_UPDATE * m_H * T / sweep_s / 1e9
     tpp = _traffic_per_pass()
+    rec = _sweep_record()
+    mhz = ck.get("sm_mhz") if isinstance(ck, dict) else None
+    issue_floor = (rec["warp_instructions_per_class"] / 4.0 / (mhz * 1e6) * 1e9
+                   if rec and rec.get("warp_instructions_per_class") and mhz else None)
     C = info["classes"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -680,9 +689,12 @@ def main():
                      "launch_ms": sweep_s * 1e3, "bytes_per_update": BYTES_PER_UPDATE,
                      "sweep_kernel": info["sweep_kernel"], "edges_per_thread": info["edges_per_thread"],
                      "chain": {"classes_per_pass": C, "ns_per_class": sweep_s / T / max(C, 1) * 1e9,
+                               "issue_floor_ns_per_class": issue_floor,
                                "note": "each class waits for the previous one (Delta(H) >= n_H - 3 "
                                        "classes on this near-clique core): the pass is bound by the "
-                                       "per-class chain on one SM, not by HBM"}},
+                                       "per-class chain on one SM, not by HBM; the issue floor is "
+                                       "the class's warp instructions (ncu) over 4 schedulers at "
+                                       "the sampled SM clock"}},
         "e2e": {"value": m_H * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
         "stages_ms": stages,
