@@ -59,8 +59,9 @@ def _sweep_hash():
         s = f.read()
     parts = []
     for a, b in (("struct TmaLayout {", "// The same staging as k_sweep_tma"),
-                 ("cudaError_t launch_sweep_tma(", "cudaError_t launch_sweep_flow(")):
-        i, j = s.find(a), s.find(b)
+                 ("cudaError_t launch_sweep_tma(", "\n}\n")):   # the launcher, to its closing brace
+        i = s.find(a)
+        j = s.find(b, i) if i >= 0 else -1
         if i < 0 or j < i:
             return "missing"
         parts.append(s[i:j])
