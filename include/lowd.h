@@ -456,6 +456,15 @@ const char* lowd_last_error(lowd_handle h);
  * all threads).  A diagnostic for benchmarks; it has no counterpart in the paper. */
 uint64_t lowd_launch_count(void);
 
+/* Failure-detection self-test of the bounded grid barrier that the cooperative kernels (grid
+ * steps of the streamed schedule, star steps, level colouring) meet at between steps: two
+ * blocks are launched on a barrier that expects three, so nothing opens it; with a short spin
+ * limit the wait must expire, set bit 1 (value 2) of the kernel's error word and end the
+ * kernel.  *err_bits receives that word; returns LOWD_OK once the kernel has ended (the
+ * context stays usable), LOWD_ERR_INVALID_ARG for a NULL err_bits, LOWD_ERR_OUT_OF_MEMORY or
+ * LOWD_ERR_CUDA if it could not run.  Uses the default stream.  No counterpart in the paper. */
+lowd_status lowd_selftest_barrier_timeout(int32_t* err_bits);
+
 #ifdef __cplusplus
 }
 #endif

@@ -139,7 +139,8 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const volatile unsigned* p) {
 // ordered before it, and lets the last arriver see every other block's); the last arriver
 // re-arms the counter and opens the generation with a release; the others poll it with
 // acquire loads.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks, int32_t* err) {
+__device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks, int32_t* err,
+                                             uint32_t max_spins = kGridSpins) {
     __syncthreads();
     bool ok = true;
     if (threadIdx.x == 0) {
@@ -152,7 +153,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
         } else {
             uint32_t spins = 0;
             while (ld_acquire_gpu(gen) == g) {
-                if (++spins > kGridSpins) { ok = false; atomicOr(err, 2); break; }
+                if (++spins > max_spins) { ok = false; atomicOr(err, 2); break; }
                 if (spins > 4096) __nanosleep(64);   // poll fast at first, then back off
             }
         }

@@ -739,3 +739,42 @@ cudaError_t lowd_star_pass(lowd_ctx* h) {
     lowd_note_launch();
     return e;
 }
+
+// ------------------------------------------------------------------ failure-detection self-test
+
+namespace {
+
+__global__ void k_barrier_selftest(unsigned* bar, unsigned nblocks, uint32_t spins, int32_t* err) {
+    grid_barrier(bar, bar + 1, nblocks, err, spins);
+}
+
+}  // namespace
+
+extern "C" lowd_status lowd_selftest_barrier_timeout(int32_t* err_bits) {
+    if (!err_bits) return LOWD_ERR_INVALID_ARG;
+    *err_bits = 0;
+    unsigned* d = nullptr;
+    if (cudaMalloc((void**)&d, 4 * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return LOWD_ERR_OUT_OF_MEMORY;
+    }
+    cudaError_t e = cudaMemset(d, 0, 4 * sizeof(unsigned));
+    unsigned* bar = d;
+    int32_t* err = reinterpret_cast<int32_t*>(d + 2);
+    unsigned expected = 3;           // two blocks arrive: the barrier can never open
+    uint32_t spins = 1u << 16;       // a short limit: the wait ends in milliseconds
+    void* args[] = {&bar, &expected, &spins, &err};
+    if (e == cudaSuccess)
+        e = cudaLaunchCooperativeKernel((const void*)k_barrier_selftest, dim3(2), dim3(32), args, 0, nullptr);
+    lowd_note_launch();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    int32_t v = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&v, err, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LOWD_ERR_CUDA;
+    }
+    *err_bits = v;
+    return LOWD_OK;
+}

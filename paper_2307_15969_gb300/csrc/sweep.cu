@@ -1247,8 +1247,10 @@ lowd_status lowd_sweep_run(lowd_ctx* h, int32_t k, const lowd_options* opt, lowd
         LOWD_CK(cudaStreamSynchronize(h->st));
         const int32_t kerr = *(int32_t*)(h->h_pin + 8);
         if (kerr != 0) {
-            snprintf(h->err, sizeof(h->err), "%s", (kerr & 4) ? "sweep: a read descriptor pointed outside the stages"
-                                                               : "sweep: a bounded wait on a staged copy expired");
+            snprintf(h->err, sizeof(h->err), "%s",
+                     (kerr & 4) ? "sweep: a read descriptor pointed outside the stages"
+                                : ((kerr & 2) ? "sweep: a bounded grid barrier expired"
+                                              : "sweep: a bounded wait on a staged copy expired"));
             return LOWD_ERR_CUDA;
         }
         done += step;

@@ -39,6 +39,7 @@ EXPORTED = (
     "lowd_ldd_dks_bound", "lowd_mpnn_param_count", "lowd_mpnn_create", "lowd_mpnn_set_params",
     "lowd_mpnn_get_params", "lowd_mpnn_bind", "lowd_mpnn_set_features", "lowd_mpnn_forward", "lowd_mpnn_backward", "lowd_mpnn_adam",
     "lowd_mpnn_read", "lowd_warm_start", "lowd_mpnn_last_error", "lowd_mpnn_free",
+    "lowd_selftest_barrier_timeout",
 )
 LOWD_MPNN_SIGMA = 1
 LOWD_MPNN_LOADS = 2
@@ -156,6 +157,8 @@ def load_library(path: str = LIB_PATH):
     lib.lowd_last_error.argtypes = [P]
     lib.lowd_launch_count.restype = C.c_uint64
     lib.lowd_launch_count.argtypes = []
+    lib.lowd_selftest_barrier_timeout.restype = i32
+    lib.lowd_selftest_barrier_timeout.argtypes = [C.POINTER(i32)]
     lib.lowd_batch_create.restype = i32
     lib.lowd_batch_create.argtypes = [i32, P, P, P, P, i32, P, C.POINTER(P)]
     lib.lowd_batch_run.restype = i32
@@ -185,6 +188,13 @@ def lowd_status_string(status: int) -> str:
 def lowd_launch_count() -> int:
     """Kernels launched by the library so far in this process."""
     return int(load_library().lowd_launch_count())
+
+
+def lowd_selftest_barrier_timeout():
+    """The bounded grid barrier's expiry path (see include/lowd.h); returns (status, error word)."""
+    bits = C.c_int32()
+    s = load_library().lowd_selftest_barrier_timeout(C.byref(bits))
+    return s, bits.value
 
 
 def _is_torch(x) -> bool:

@@ -452,3 +452,20 @@ def test_splits_checkpoint_resume(pkg, orc):
     l60b = _np(pkg.lowd_get_loads(h2))
     assert np.max(np.abs(l60 - l60b)) <= 1e-5 * l60.max()
     pkg.lowd_free(h1); pkg.lowd_free(h2)
+
+
+def test_bounded_grid_barrier_expires_and_reports(pkg):
+    """Failure detection without a GPU fault: a grid barrier that nothing can open (two blocks,
+    three expected) must give up after its spin limit, set its error bit and end the kernel;
+    the context then keeps working."""
+    import time
+    t0 = time.perf_counter()
+    status, bits = pkg.lowd_selftest_barrier_timeout()
+    assert status == pkg.LOWD_OK and (bits & 2) == 2, (status, bits)
+    assert time.perf_counter() - t0 < 30.0
+    g = synth.small_family("clique", 8)
+    h = _load(pkg, g, False)
+    st = pkg.lowd_iterate(h, 50, check_every=10, rel_tol=1e-9)
+    S, rho, _ = pkg.lowd_extract(h)
+    assert abs(rho - 3.5) < 1e-9 and len(S) == 8
+    pkg.lowd_free(h)
