@@ -25,7 +25,9 @@
 // with at most 2^(k-1) nodes of degree >= 2^k.
 //
 // Execution.  One cooperative launch per pass runs every step; blocks take the stars of a
-// step, one star per block at a time, and meet at a bounded grid barrier between steps.  A
+// step, one star per block at a time, and meet at a bounded grid barrier between steps
+// (512-thread blocks, one per SM; 128-thread blocks, four per SM, when the steps average at
+// least two stars per SM, as on unpruned graphs).  A
 // block keeps up to kStarRegs edges per thread in registers (the rest of a large star in a
 // scratch array) and solves g(lam) = 0 inside a shrinking bracket, by Newton steps and (when
 // a Newton step leaves the bracket) Illinois secant steps (star_root); each evaluation of g
