@@ -82,7 +82,8 @@ typedef struct {
                              Default 0 (kernel 1: on dense cores whose hubs appear in every
                              class it is faster, as waiting warps sleep at the barrier) */
     int32_t hub_stars;    /* hub-star block updates (read when the schedule is built, i.e. by
-                             the first lowd_iterate of a graph): 0 = off (default); 1 =
+                             the first lowd_iterate of a graph; a schedule built earlier by
+                             lowd_set_splits or lowd_warm_start has none): 0 = off (default); 1 =
                              automatic threshold; t >= 2 = threshold.  Nodes of (unweighted)
                              degree >= t are hubs; an edge with exactly one hub end is a star
                              edge.  A pass runs Algorithm 1 over the other edges in the
