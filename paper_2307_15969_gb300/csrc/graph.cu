@@ -314,7 +314,7 @@ __device__ __forceinline__ int32_t rank_of(uint2 p, int32_t x) {
 }
 
 template <bool RELABEL>
-__global__ void __launch_bounds__(kT)
+__global__ void __launch_bounds__(kT, 4)
 k_prune_edges(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
               const int64_t* __restrict__ ew, int64_t me, const uint32_t* __restrict__ dead,
               const uint2* __restrict__ rank_words, const unsigned long long* __restrict__ removed,
@@ -333,13 +333,25 @@ k_prune_edges(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
         int32_t a[kPruneItems], b[kPruneItems];
         int64_t x[kPruneItems];
         unsigned keepm = 0;
-#pragma unroll
-        for (int i = 0; i < kPruneItems; ++i) {
+        auto load = [&](int i) {
             const int64_t e = tb + (int64_t)i * kT + threadIdx.x;
             const bool ok = e < me;
             a[i] = ok ? eu[e] : -1;
             b[i] = ok ? ev[e] : -1;
             x[i] = ok ? (ew ? ew[e] : 1) : 0;
+        };
+        // later rounds (lookups mostly in L1): the tile's ends first, so that their loads
+        // overlap; the first round keeps one item's loads at a time (its rank words need the
+        // registers, and its random lookups set its pace)
+        if (!RELABEL) {
+#pragma unroll
+            for (int i = 0; i < kPruneItems; ++i) load(i);
+        }
+#pragma unroll
+        for (int i = 0; i < kPruneItems; ++i) {
+            const int64_t e = tb + (int64_t)i * kT + threadIdx.x;
+            const bool ok = e < me;
+            if (RELABEL) load(i);
             bool ra, rb;
             int32_t na = 0, nb = 0;   // RELABEL: the ends' ids among the survivors
             if (RELABEL) {
